@@ -1,0 +1,360 @@
+"""Throughput of the AIDW hot path (grid build + grid kNN + all-points
+weighting) on GB300, printed as one JSON line.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+A step is one pass of the whole path over one batch: build the even grid of
+the data points, find every query's k nearest neighbours, compute alpha and
+the weighted prediction of Eq. 1 over all data points.  The default workload
+is n = m = 1,048,576 points uniform in [0,1000]^2, k = 10, float32 with
+compensated sums (AIDW_FP32_COMP).
+
+Under torchrun (N > 1) every rank runs the same-sized workload on its own
+GPU with its own seeded queries against the same data (weak scaling: the
+queries shard, nothing is exchanged on the data path); rank 0 prints the
+total over ranks divided by the slowest rank's time.
+
+``--impl reference`` times the FP64 CPU oracle (the only reference this
+method has) on the host cores, each step a bounded sample of the queries.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "AIDW interpolated points/s at n=m=1M (kNN+weighting), FP32-comp vs FP64 plain"
+UNIT = "points/s"
+L2_FLUSH_BYTES = 256 << 20
+# SFU (XU pipe) results per SM per clock on GB300.  Derived from ncu: the
+# weighting kernel issues 18 lg2/ex2 per SM per clock and ncu reports the XU
+# pipe at 56.5 % of its peak, i.e. a peak of 32 per SM per clock.
+MUFU_PER_SM_CLK = 32
+MUFU_PER_PAIR = 2         # one lg2 and one ex2 per (query, data point) pair
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=("ours", "reference"), default="ours")
+    ap.add_argument("--n", type=int, default=1 << 20, help="data points = queries")
+    ap.add_argument("--k", type=int, default=10)
+    ap.add_argument("--workload", choices=("uniform", "clustered"), default="uniform")
+    ap.add_argument("--e2e-steps", type=int, default=3)
+    ap.add_argument("--fp64-queries", type=int, default=16384)
+    ap.add_argument("--cpu-seconds", type=float, default=15.0)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    return ap.parse_args()
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+def make_workload(args, rank):
+    from paper_1601_05904_gb300 import inputs
+    if args.workload == "uniform":
+        w = inputs.uniform_kilo(n=args.n, k=args.k, seed=1)
+    else:
+        w = inputs.clustered_kilo(n=args.n, k=args.k, seed=2)
+    if rank:
+        # each rank its own queries over the same data (weak scaling)
+        rng = np.random.default_rng(10_000 + rank)
+        w.qx, w.qy = inputs.uniform_points(rng, w.m, 0.0, inputs.SIDE_KILO)
+    return w
+
+
+def workload_config(args, world, precision=None):
+    return {"workload": f"{args.workload} n=m={args.n} in [0,1000]^2, k={args.k}, "
+                        "alpha levels 1..5, R_min/R_max 0/2",
+            "n_data": args.n, "n_query_per_gpu": args.n, "k": args.k,
+            "precision": precision or "FP32-comp (SFU exp2/log2, TwoSum-compensated f32 "
+                                      "sums, f64 alpha)",
+            "l2": f"flushed between timed steps ({L2_FLUSH_BYTES >> 20} MiB write)",
+            "parallelism": f"query-sharded x{world}" if world > 1 else "single GPU"}
+
+
+class ClockSampler:
+    """nvidia-smi clock / throttle sampling during the timed region."""
+
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        try:
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            os.close(fd)
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        out = {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "samples": 0}
+        if self.proc is None:
+            return out
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        rows = []
+        with open(self.path) as f:
+            for line in f:
+                parts = [p.strip() for p in line.split(",")]
+                if len(parts) >= 8:
+                    rows.append(parts)
+        os.unlink(self.path)
+        if not rows:
+            return out
+
+        def num(v):
+            try:
+                return float(v)
+            except ValueError:
+                return None
+        sm = [num(r[0]) for r in rows if num(r[0]) is not None]
+        mx = [num(r[1]) for r in rows if num(r[1]) is not None]
+        names = ("hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap")
+        reasons = sorted({names[i] for r in rows for i in range(4)
+                          if r[4 + i].lower() == "active"})
+        out.update(sm_mhz=statistics.median(sm) if sm else None,
+                   sm_max_mhz=max(mx) if mx else None, reasons=reasons, samples=len(rows),
+                   power_w_max=max((num(r[2]) or 0.0) for r in rows))
+        return out
+
+
+def measured_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as f:
+            return json.load(f)
+    return None
+
+
+def cpu_baseline(w, seconds: float, rank: int):
+    """The oracle as it stands, on the host cores, over a bounded query sample."""
+    import oracle
+    from paper_1601_05904_gb300 import inputs
+    oracle.build()
+    cores = oracle.num_threads()
+    probe = max(cores, 8)
+    s = inputs.query_subsample(w.m, probe, seed=2024 + rank)
+    t0 = time.perf_counter()
+    oracle.aidw(w.x, w.y, w.z, w.qx[s], w.qy[s], w.k)
+    per_q = (time.perf_counter() - t0) / probe
+    count = int(max(probe, min(w.m, seconds / max(per_q, 1e-9))))
+    s = inputs.query_subsample(w.m, count, seed=4048 + rank)
+    t0 = time.perf_counter()
+    oracle.aidw(w.x, w.y, w.z, w.qx[s], w.qy[s], w.k)
+    dt = time.perf_counter() - t0
+    return {"value": count / dt, "unit": UNIT, "cores": cores, "kind": "oracle",
+            "sample": f"{count} of {w.m} queries against all {w.n} data points "
+                      f"({dt:.1f} s, FP64, brute-force kNN with full sort)"}
+
+
+def run_reference(args):
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return 0
+    w = make_workload(args, 0)
+    import oracle
+    from paper_1601_05904_gb300 import inputs
+    oracle.build()
+    cores = oracle.num_threads()
+    per_step = max(cores, 16)
+    for i in range(args.warmup):
+        s = inputs.query_subsample(w.m, per_step, seed=500 + i)
+        oracle.aidw(w.x, w.y, w.z, w.qx[s], w.qy[s], w.k)
+    times = []
+    for i in range(args.steps):
+        s = inputs.query_subsample(w.m, per_step, seed=900 + i)
+        t0 = time.perf_counter()
+        oracle.aidw(w.x, w.y, w.z, w.qx[s], w.qy[s], w.k)
+        times.append(time.perf_counter() - t0)
+    total = sum(times)
+    value = per_step * args.steps / total
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT,
+            "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": 1000.0 * total / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": workload_config(args, 1, "FP64 CPU oracle (brute-force kNN, pow)"),
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
+                             "sample": f"{per_step} queries per step against all {w.n} "
+                                       "data points"},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def run_ours(args):
+    import torch
+
+    import paper_1601_05904_gb300 as pkg
+    from paper_1601_05904_gb300 import binding
+
+    rank, world, local = dist_env()
+    if not torch.cuda.is_available():
+        raise RuntimeError("bench.py needs a CUDA device")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=dev)
+    binding.load()
+
+    w = make_workload(args, rank)
+    params = pkg.Params(k=w.k, cell_scale=0.0)
+    t = {k: torch.from_numpy(getattr(w, k)).to(dev) for k in ("x", "y", "z", "qx", "qy")}
+    out_z = torch.empty(w.m, dtype=torch.float32, device=dev)
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
+
+    def step():
+        g = binding.aidw_grid_build(t["x"], t["y"], t["z"], params)
+        binding.aidw_interpolate(g, t["qx"], t["qy"], params, out_z=out_z)
+        g.destroy()
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    binding.aidw_profile_read()
+
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+          for _ in range(args.steps)]
+    clocks = ClockSampler(local)
+    if world > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    clocks.start()
+    binding.aidw_profile_enable(True)
+    t_wall = time.perf_counter()
+    for i in range(args.steps):
+        flush.fill_(float(i))
+        ev[i][0].record()
+        step()
+        ev[i][1].record()
+    torch.cuda.synchronize()
+    wall = time.perf_counter() - t_wall
+    binding.aidw_profile_enable(False)
+    if world > 1:
+        torch.distributed.barrier()
+    clk = clocks.stop()
+    stage = binding.aidw_profile_read()
+    step_ms = sum(a.elapsed_time(b) for a, b in ev) / args.steps
+    my_s = step_ms * args.steps / 1000.0
+    if world > 1:
+        tt = torch.tensor([my_s], dtype=torch.float64, device=dev)
+        torch.distributed.all_reduce(tt, op=torch.distributed.ReduceOp.MAX)
+        my_s = float(tt.item())
+    value = world * w.m * args.steps / my_s
+    launches = sum(v[1] for v in stage.values())
+
+    # float64 plain path on a query sample (kNN + weighting + grid build)
+    fp64 = None
+    if args.fp64_queries > 0 and rank == 0:
+        mq = min(args.fp64_queries, w.m)
+        p64 = pkg.Params(k=w.k, precision=binding.AIDW_FP64_PLAIN)
+        qx64, qy64 = t["qx"][:mq].contiguous(), t["qy"][:mq].contiguous()
+        g = binding.aidw_grid_build(t["x"], t["y"], t["z"], p64)
+        binding.aidw_interpolate(g, qx64, qy64, p64)
+        torch.cuda.synchronize()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record()
+        binding.aidw_interpolate(g, qx64, qy64, p64)
+        b.record()
+        torch.cuda.synchronize()
+        g.destroy()
+        ms = a.elapsed_time(b)
+        fp64 = {"value": mq / (ms / 1000.0), "unit": UNIT,
+                "sample": f"first {mq} of {w.m} queries against all {w.n} data points "
+                          "(kNN + weighting, grid prebuilt)",
+                "ms": ms}
+
+    # end to end through the public API from pinned host buffers
+    e2e = None
+    if not args.no_e2e and args.e2e_steps > 0:
+        host = {k: torch.from_numpy(getattr(w, k)).pin_memory() for k in ("x", "y", "z", "qx", "qy")}
+        binding.interpolate_host(host["x"], host["y"], host["z"], host["qx"], host["qy"], params)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for _ in range(args.e2e_steps):
+            zh = binding.interpolate_host(host["x"], host["y"], host["z"], host["qx"],
+                                          host["qy"], params)
+            float(zh[0])
+        e2e_s = time.perf_counter() - t0
+        h2d = sum(v.numel() * 4 for v in host.values())
+        e2e = {"value": w.m * args.e2e_steps / e2e_s, "unit": UNIT,
+               "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(w.m * 4),
+               "ms_per_step": 1000.0 * e2e_s / args.e2e_steps}
+
+    if rank != 0:
+        if world > 1:
+            torch.distributed.destroy_process_group()
+        return 0
+
+    props = torch.cuda.get_device_properties(dev)
+    peaks = measured_peaks() or {}
+    sm_max = float(peaks.get("sm_max_mhz", 2070.0))
+    w_ms, w_launches = stage["weight"]
+    pairs = float(w.n) * float(w.m)
+    achieved = pairs / (w_ms / w_launches / 1000.0) / 1e9 if w_launches else None
+    peak = MUFU_PER_SM_CLK * props.multi_processor_count * sm_max * 1e6 / MUFU_PER_PAIR / 1e9
+    roofline = {"bound": "alu", "kernel": "k_weight_f32 (all-points weighting, Eq. 1)",
+                "achieved": achieved, "peak": peak, "unit": "Gpair/s",
+                "frac": (achieved / peak) if achieved else None, "traffic": None,
+                "peak_basis": f"SFU issue: {MUFU_PER_SM_CLK} lg2/ex2 per SM per clock x "
+                              f"{props.multi_processor_count} SMs x {sm_max:.0f} MHz max clock / "
+                              f"{MUFU_PER_PAIR} SFU ops per pair"}
+    stages_ms = {k: v[0] / args.steps for k, v in stage.items()}
+    cpu = None
+    if not args.no_cpu_baseline and world >= 1:
+        cpu = cpu_baseline(w, args.cpu_seconds, rank)
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": step_ms,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+            "data": "synthetic", "config": workload_config(args, world),
+            "e2e": e2e, "gpu_launches": int(launches), "roofline": roofline,
+            "cpu_baseline": cpu, "fp64_plain": fp64,
+            "stages_ms_per_step": stages_ms, "wall_s_timed": wall,
+            "clocks": clk, "device": props.name}
+    print(json.dumps(line), flush=True)
+    if world > 1:
+        torch.distributed.destroy_process_group()
+    return 0
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_ours(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,179 @@
+/*
+ * aidw.h - C ABI of the GB300 (sm_103a) AIDW interpolation library.
+ *
+ * Adaptive inverse distance weighting with an even-grid kNN search, after
+ * Mei, Xu & Xu, "Improving GPU-accelerated Adaptive IDW Interpolation
+ * Algorithm Using Fast kNN Search" (arXiv 1601.05904).
+ *
+ * Conventions shared by every entry point
+ * ----------------------------------------
+ *  - Point sets are structure-of-arrays float32 (x[], y[], z[]), the layout
+ *    of the paper's Sec. 4.2.1.  "Data points" are the samples with known z;
+ *    "queries" are the interpolated points.
+ *  - Every array argument is a DEVICE pointer owned by the caller unless the
+ *    comment says otherwise.  The library never frees caller memory.
+ *  - Calls are asynchronous on `stream` (a cudaStream_t; NULL is the legacy
+ *    default stream).  A function that must read a device result back says
+ *    so; every other function only enqueues work.
+ *  - Arguments are validated on the host before any CUDA call; a rejected
+ *    call enqueues nothing.  Errors the device finds (non-finite input
+ *    coordinates, an expired bounded wait) are latched in the grid and
+ *    returned by aidw_grid_status() and aidw_grid_destroy().
+ *  - The library owns grid handles and per-call scratch, which it takes with
+ *    cudaMallocAsync on `stream` and returns the same way.
+ */
+#ifndef AIDW_H_
+#define AIDW_H_
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* Same type as cudaStream_t, declared here so that callers need no CUDA header. */
+typedef struct CUstream_st *aidw_stream_t;
+
+typedef enum {
+    AIDW_OK = 0,
+    AIDW_ERR_INVALID_ARG = 1, /* null pointer, negative size, bad parameter    */
+    AIDW_ERR_K_RANGE = 2,     /* k < 1, k > 32 or k > number of data points    */
+    AIDW_ERR_NONFINITE = 3,   /* a NaN or Inf coordinate or value was found    */
+    AIDW_ERR_OOM = 4,         /* a device allocation failed                    */
+    AIDW_ERR_CUDA = 5,        /* any other CUDA runtime error                  */
+    AIDW_ERR_TIMEOUT = 6      /* a bounded device-side wait expired            */
+} aidw_status;
+
+/* Arithmetic of the kNN and weighting stages.
+ *  AIDW_FP32_COMP  float32 distances, power by exp2(alpha*log2) on the SFU,
+ *                  compensated float32 sums, float64 alpha and final divide.
+ *                  Outputs are float32.
+ *  AIDW_FP64_PLAIN float64 distances, pow(), plain float64 sums.  Outputs
+ *                  are float64. */
+typedef enum { AIDW_FP32_COMP = 0, AIDW_FP64_PLAIN = 1 } aidw_precision;
+
+#define AIDW_MAX_K 32
+
+/* Parameters of the method.  aidw_params_default() fills the defaults.
+ *  k           neighbours for r_obs (Eq. 3); 1 <= k <= 32 and k <= n_data.
+ *  alpha[5]    the five distance-decay levels of Eq. 6 (finite, > 0).  The
+ *              paper gives no values; the default is {1, 2, 3, 4, 5}.
+ *  r_min/r_max bounds of the membership of Eq. 5 (paper: 0.0 and 2.0);
+ *              0 <= r_min < r_max.
+ *  area        A of Eq. 2; <= 0 selects the area of the data bounding box.
+ *  cell_scale  grid cell width = cell_scale * r_exp (the paper's width is
+ *              r_exp itself, Sec. 4.1.1, i.e. cell_scale = 1); <= 0 lets
+ *              the library choose.
+ *  precision   an aidw_precision value. */
+typedef struct {
+    int k;
+    double alpha[5];
+    double r_min;
+    double r_max;
+    double area;
+    double cell_scale;
+    int precision;
+} aidw_params;
+
+void aidw_params_default(aidw_params *p);
+
+/* Static description of a built grid (host copy). */
+typedef struct {
+    int64_t n_data;
+    int64_t n_col;      /* nCol = (int)((maxX - minX + cw) / cw), Sec. 4.1.1 */
+    int64_t n_row;
+    int64_t n_cells;    /* n_col * n_row */
+    double min_x, min_y, max_x, max_y; /* bounding box of the data points */
+    double area;        /* A used for r_exp */
+    double r_exp;       /* Eq. 2 with n = n_data */
+    double cell_width;  /* cw */
+    double cell_scale;  /* the scale the grid was built with */
+} aidw_grid_info;
+
+/* Opaque grid over a set of data points; owns its device buffers. */
+typedef struct aidw_grid aidw_grid;
+
+/* Builds the even grid of Sec. 3.2.1-3.2.3 / 4.1.1-4.1.3: bounding box,
+ * cell width (Eq. 2), nCol/nRow, a cell index per point, and a stable
+ * counting sort that stores the points in cell order with the (head, count)
+ * pair of every cell (Fig. 3).  x, y, z: [n_data] device float32; they are
+ * copied into the grid and may be freed once the stream reaches this call.
+ * Reads the device result back once (stream-synchronous) to report
+ * non-finite input as AIDW_ERR_NONFINITE.  On success *out owns the grid.
+ * Uses p->area and p->cell_scale; the other fields are ignored here. */
+aidw_status aidw_grid_build(const float *x, const float *y, const float *z, int64_t n_data,
+                            const aidw_params *p, aidw_stream_t stream, aidw_grid **out);
+
+/* Frees the grid after draining the stream it was built on.  Returns the
+ * latched device status (AIDW_OK if none). */
+aidw_status aidw_grid_destroy(aidw_grid *g);
+
+/* Host copy of the grid's dimensions (synchronises with the build stream). */
+aidw_status aidw_grid_get_info(const aidw_grid *g, aidw_grid_info *info);
+
+/* Copies the grid's cell heads and cell-ordered permutation into caller
+ * device buffers: cell_start [n_cells + 1] (head of cell c; count of c is
+ * cell_start[c+1] - cell_start[c]) and perm [n_data] (original index of the
+ * point stored at each position; stable within a cell).  Either may be NULL. */
+aidw_status aidw_grid_export(const aidw_grid *g, int64_t *cell_start, int32_t *perm,
+                             aidw_stream_t stream);
+
+/* Synchronises the grid's stream and returns then clears the latched
+ * device-side error (non-finite query coordinates, expired waits). */
+aidw_status aidw_grid_status(aidw_grid *g);
+
+/* Exact k nearest neighbours of each query by the grid search of
+ * Sec. 3.2.4 / 4.1.4: locate the query's cell, visit rings of cells
+ * outwards, keep the k best squared distances (Sec. 4.1.4's remark on
+ * avoiding square roots) in a register top-k, and stop once the nearest
+ * cell outside the visited block is farther than the k-th distance (an
+ * exact rule in place of the paper's "one extra level", which can miss
+ * neighbours).  Distances are float32 (Euclidean, from float32 squared
+ * distances).  Ties are ordered by original index.
+ *  qx, qy    [n_query] device float32
+ *  out_idx   [n_query * k] int32 original indices, row-major by query,
+ *            increasing distance; or NULL
+ *  out_dist  [n_query * k] float32 distances; or NULL
+ *  out_robs  [n_query] float32 r_obs of Eq. 3; or NULL
+ * A query with a NaN/Inf coordinate gets idx -1, NaN distances and latches
+ * AIDW_ERR_NONFINITE in the grid. */
+aidw_status aidw_knn(const aidw_grid *g, const float *qx, const float *qy, int64_t n_query,
+                     int k, int32_t *out_idx, float *out_dist, float *out_robs,
+                     aidw_stream_t stream);
+
+/* AIDW prediction of every query: kNN (above), then per query r_exp
+ * (Eq. 2), R (Eq. 4), mu (Eq. 5) and alpha (Eq. 6), then Eq. 1 summed over
+ * ALL data points of the grid.  A query at distance 0 from data points
+ * returns the mean z of those points (the limit of Eq. 1).
+ *  out_z      [n_query] predictions: float32 for AIDW_FP32_COMP, float64
+ *             for AIDW_FP64_PLAIN
+ *  out_alpha  [n_query] alpha of each query, same element type; or NULL
+ * p->area (when > 0) overrides the area the grid was built with. */
+aidw_status aidw_interpolate(const aidw_grid *g, const float *qx, const float *qy,
+                             int64_t n_query, const aidw_params *p, void *out_z,
+                             void *out_alpha, aidw_stream_t stream);
+
+/* Short English name of a status code (static storage). */
+const char *aidw_status_string(aidw_status s);
+
+/* ---- stage timing ---------------------------------------------------------
+ * When enabled, every call records CUDA events around each stage it
+ * launches on its stream.  aidw_profile_read() waits for those events, adds
+ * the elapsed milliseconds and launch counts per stage into ms[] and
+ * launches[] (each AIDW_STAGE_COUNT long), then clears the record. */
+typedef enum {
+    AIDW_STAGE_GRID_BUILD = 0, /* bounding box .. cell-ordered points      */
+    AIDW_STAGE_KNN = 1,        /* grid kNN + alpha                         */
+    AIDW_STAGE_WEIGHT = 2,     /* all-points weighting (Eq. 1), stream-K   */
+    AIDW_STAGE_FINALIZE = 3,   /* combine partial sums, divide             */
+    AIDW_STAGE_COUNT = 4
+} aidw_stage;
+
+aidw_status aidw_profile_enable(int on);
+aidw_status aidw_profile_read(double *ms, int64_t *launches);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* AIDW_H_ */

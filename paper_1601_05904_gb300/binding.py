@@ -1,0 +1,295 @@
+"""Python binding of the C ABI in ``include/aidw.h`` (ctypes, marshalling only).
+
+Every function here has the name of the C entry point it calls and does
+nothing but check tensor arguments, pass device pointers and the current
+CUDA stream, and turn status codes into exceptions.  All computation runs in
+``libaidw.so``; if the library is missing this module raises instead of
+falling back to anything else.
+
+Tensors are torch CUDA tensors (torch is used for device memory and streams
+only): float32, contiguous, on the current device.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+from dataclasses import dataclass, field
+
+PKG = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(PKG, "libaidw.so")
+
+AIDW_OK = 0
+AIDW_FP32_COMP = 0
+AIDW_FP64_PLAIN = 1
+AIDW_MAX_K = 32
+STAGES = ("grid_build", "knn", "weight", "finalize")
+
+_STATUS_NAMES = {0: "AIDW_OK", 1: "AIDW_ERR_INVALID_ARG", 2: "AIDW_ERR_K_RANGE",
+                 3: "AIDW_ERR_NONFINITE", 4: "AIDW_ERR_OOM", 5: "AIDW_ERR_CUDA",
+                 6: "AIDW_ERR_TIMEOUT"}
+
+
+class AidwError(RuntimeError):
+    def __init__(self, status: int, where: str):
+        self.status = status
+        super().__init__(f"{where}: {_STATUS_NAMES.get(status, status)} "
+                         f"({aidw_status_string(status)})")
+
+
+class CParams(ctypes.Structure):
+    _fields_ = [("k", ctypes.c_int), ("alpha", ctypes.c_double * 5),
+                ("r_min", ctypes.c_double), ("r_max", ctypes.c_double),
+                ("area", ctypes.c_double), ("cell_scale", ctypes.c_double),
+                ("precision", ctypes.c_int)]
+
+
+class CGridInfo(ctypes.Structure):
+    _fields_ = [("n_data", ctypes.c_int64), ("n_col", ctypes.c_int64),
+                ("n_row", ctypes.c_int64), ("n_cells", ctypes.c_int64),
+                ("min_x", ctypes.c_double), ("min_y", ctypes.c_double),
+                ("max_x", ctypes.c_double), ("max_y", ctypes.c_double),
+                ("area", ctypes.c_double), ("r_exp", ctypes.c_double),
+                ("cell_width", ctypes.c_double), ("cell_scale", ctypes.c_double)]
+
+
+@dataclass
+class Params:
+    """Mirror of aidw_params (defaults as aidw_params_default)."""
+    k: int = 10
+    alpha: tuple = (1.0, 2.0, 3.0, 4.0, 5.0)
+    r_min: float = 0.0
+    r_max: float = 2.0
+    area: float = 0.0
+    cell_scale: float = 0.0
+    precision: int = AIDW_FP32_COMP
+
+    def to_c(self) -> CParams:
+        c = CParams()
+        c.k = int(self.k)
+        for i, a in enumerate(self.alpha):
+            c.alpha[i] = float(a)
+        c.r_min = float(self.r_min)
+        c.r_max = float(self.r_max)
+        c.area = float(self.area)
+        c.cell_scale = float(self.cell_scale)
+        c.precision = int(self.precision)
+        return c
+
+
+_lib = None
+_lock = threading.Lock()
+
+
+def load(path: str | None = None):
+    """Load libaidw.so (built in-tree by ``paper_1601_05904_gb300.build``)."""
+    global _lib
+    with _lock:
+        if _lib is not None:
+            return _lib
+        p = path or LIB_PATH
+        if not os.path.exists(p):
+            raise RuntimeError(f"{p} is missing: build the CUDA library first "
+                               "(python -c 'import __graft_entry__ as g; g.build()')")
+        lib = ctypes.CDLL(p)
+        vp, i64, c_int = ctypes.c_void_p, ctypes.c_int64, ctypes.c_int
+        P = ctypes.POINTER
+        lib.aidw_params_default.restype = None
+        lib.aidw_params_default.argtypes = [P(CParams)]
+        lib.aidw_status_string.restype = ctypes.c_char_p
+        lib.aidw_status_string.argtypes = [c_int]
+        lib.aidw_grid_build.restype = c_int
+        lib.aidw_grid_build.argtypes = [vp, vp, vp, i64, P(CParams), vp, P(vp)]
+        lib.aidw_grid_destroy.restype = c_int
+        lib.aidw_grid_destroy.argtypes = [vp]
+        lib.aidw_grid_get_info.restype = c_int
+        lib.aidw_grid_get_info.argtypes = [vp, P(CGridInfo)]
+        lib.aidw_grid_export.restype = c_int
+        lib.aidw_grid_export.argtypes = [vp, vp, vp, vp]
+        lib.aidw_grid_status.restype = c_int
+        lib.aidw_grid_status.argtypes = [vp]
+        lib.aidw_knn.restype = c_int
+        lib.aidw_knn.argtypes = [vp, vp, vp, i64, c_int, vp, vp, vp, vp]
+        lib.aidw_interpolate.restype = c_int
+        lib.aidw_interpolate.argtypes = [vp, vp, vp, i64, P(CParams), vp, vp, vp]
+        lib.aidw_profile_enable.restype = c_int
+        lib.aidw_profile_enable.argtypes = [c_int]
+        lib.aidw_profile_read.restype = c_int
+        lib.aidw_profile_read.argtypes = [P(ctypes.c_double), P(ctypes.c_int64)]
+        _lib = lib
+        return lib
+
+
+def _check(status: int, where: str):
+    if status != AIDW_OK:
+        raise AidwError(status, where)
+
+
+def _ptr(t):
+    return None if t is None else ctypes.c_void_p(t.data_ptr())
+
+
+def _stream(stream):
+    import torch
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return ctypes.c_void_p(s.cuda_stream)
+
+
+def _f32_dev(t, name: str):
+    import torch
+    if not isinstance(t, torch.Tensor) or not t.is_cuda:
+        raise TypeError(f"{name} must be a CUDA tensor")
+    if t.dtype != torch.float32 or not t.is_contiguous() or t.dim() != 1:
+        raise TypeError(f"{name} must be a contiguous 1-D float32 tensor")
+    return t
+
+
+def aidw_status_string(status: int) -> str:
+    if _lib is None:
+        return _STATUS_NAMES.get(status, str(status))
+    return _lib.aidw_status_string(int(status)).decode()
+
+
+def aidw_params_default() -> Params:
+    c = CParams()
+    load().aidw_params_default(ctypes.byref(c))
+    return Params(k=c.k, alpha=tuple(c.alpha), r_min=c.r_min, r_max=c.r_max, area=c.area,
+                  cell_scale=c.cell_scale, precision=c.precision)
+
+
+@dataclass
+class Grid:
+    """Owner of an aidw_grid handle; destroy() (or garbage collection) frees it."""
+    handle: ctypes.c_void_p
+    n_data: int
+    _alive: bool = field(default=True, repr=False)
+
+    def destroy(self) -> None:
+        if self._alive:
+            self._alive = False
+            _check(load().aidw_grid_destroy(self.handle), "aidw_grid_destroy")
+
+    def __del__(self):
+        if getattr(self, "_alive", False):
+            try:
+                self._alive = False
+                load().aidw_grid_destroy(self.handle)
+            except Exception:
+                pass
+
+
+def aidw_grid_build(x, y, z, params: Params | None = None, stream=None) -> Grid:
+    x, y, z = _f32_dev(x, "x"), _f32_dev(y, "y"), _f32_dev(z, "z")
+    if not (x.numel() == y.numel() == z.numel()):
+        raise ValueError("x, y, z must have the same length")
+    p = (params or Params()).to_c()
+    h = ctypes.c_void_p()
+    _check(load().aidw_grid_build(_ptr(x), _ptr(y), _ptr(z), x.numel(), ctypes.byref(p),
+                                  _stream(stream), ctypes.byref(h)), "aidw_grid_build")
+    return Grid(h, x.numel())
+
+
+def aidw_grid_destroy(grid: Grid) -> None:
+    grid.destroy()
+
+
+def aidw_grid_get_info(grid: Grid) -> dict:
+    info = CGridInfo()
+    _check(load().aidw_grid_get_info(grid.handle, ctypes.byref(info)), "aidw_grid_get_info")
+    return {name: getattr(info, name) for name, _ in CGridInfo._fields_}
+
+
+def aidw_grid_export(grid: Grid, stream=None):
+    """Returns (cell_start int64 [n_cells+1], perm int32 [n_data]) device tensors."""
+    import torch
+    info = aidw_grid_get_info(grid)
+    cs = torch.empty(info["n_cells"] + 1, dtype=torch.int64, device="cuda")
+    perm = torch.empty(grid.n_data, dtype=torch.int32, device="cuda")
+    _check(load().aidw_grid_export(grid.handle, _ptr(cs), _ptr(perm), _stream(stream)),
+           "aidw_grid_export")
+    return cs, perm
+
+
+def aidw_grid_status(grid: Grid) -> int:
+    """Synchronises and returns the latched device status code (0 = ok)."""
+    return int(load().aidw_grid_status(grid.handle))
+
+
+def aidw_knn(grid: Grid, qx, qy, k: int, out_idx=None, out_dist=None, out_robs=None,
+             want=("idx", "dist", "robs"), stream=None):
+    """Grid kNN.  Allocates the outputs named in ``want`` that are not given.
+    Returns (idx int32 [m,k] | None, dist float32 [m,k] | None, robs float32 [m] | None)."""
+    import torch
+    qx, qy = _f32_dev(qx, "qx"), _f32_dev(qy, "qy")
+    m = qx.numel()
+    if qy.numel() != m:
+        raise ValueError("qx and qy must have the same length")
+    if out_idx is None and "idx" in want:
+        out_idx = torch.empty((m, k), dtype=torch.int32, device=qx.device)
+    if out_dist is None and "dist" in want:
+        out_dist = torch.empty((m, k), dtype=torch.float32, device=qx.device)
+    if out_robs is None and "robs" in want:
+        out_robs = torch.empty(m, dtype=torch.float32, device=qx.device)
+    _check(load().aidw_knn(grid.handle, _ptr(qx), _ptr(qy), m, int(k), _ptr(out_idx),
+                           _ptr(out_dist), _ptr(out_robs), _stream(stream)), "aidw_knn")
+    return out_idx, out_dist, out_robs
+
+
+def aidw_interpolate(grid: Grid, qx, qy, params: Params | None = None, out_z=None,
+                     out_alpha=None, want_alpha: bool = False, stream=None):
+    """AIDW predictions.  Output dtype is float32 (FP32_COMP) or float64
+    (FP64_PLAIN).  Returns (z, alpha | None)."""
+    import torch
+    p = params or Params()
+    qx, qy = _f32_dev(qx, "qx"), _f32_dev(qy, "qy")
+    m = qx.numel()
+    if qy.numel() != m:
+        raise ValueError("qx and qy must have the same length")
+    dt = torch.float64 if p.precision == AIDW_FP64_PLAIN else torch.float32
+    if out_z is None:
+        out_z = torch.empty(m, dtype=dt, device=qx.device)
+    if out_alpha is None and want_alpha:
+        out_alpha = torch.empty(m, dtype=dt, device=qx.device)
+    for t, name in ((out_z, "out_z"), (out_alpha, "out_alpha")):
+        if t is not None and (t.dtype != dt or t.numel() != m or not t.is_contiguous()):
+            raise TypeError(f"{name} must be a contiguous {dt} tensor of length {m}")
+    pc = p.to_c()
+    _check(load().aidw_interpolate(grid.handle, _ptr(qx), _ptr(qy), m, ctypes.byref(pc),
+                                   _ptr(out_z), _ptr(out_alpha), _stream(stream)),
+           "aidw_interpolate")
+    return out_z, out_alpha
+
+
+def aidw_profile_enable(on: bool = True) -> None:
+    _check(load().aidw_profile_enable(1 if on else 0), "aidw_profile_enable")
+
+
+def aidw_profile_read() -> dict:
+    """Per stage: (total ms, kernel launches) since the last read."""
+    ms = (ctypes.c_double * len(STAGES))()
+    ln = (ctypes.c_int64 * len(STAGES))()
+    _check(load().aidw_profile_read(ms, ln), "aidw_profile_read")
+    return {s: (ms[i], int(ln[i])) for i, s in enumerate(STAGES)}
+
+
+def interpolate_host(x, y, z, qx, qy, params: Params | None = None, stream=None):
+    """End-to-end call from host arrays: copies the inputs to the device,
+    builds the grid, interpolates and copies the predictions back.
+
+    Inputs may be numpy arrays or CPU tensors (pinned tensors copy
+    asynchronously).  Returns a CPU tensor of predictions."""
+    import torch
+    dev = torch.device("cuda", torch.cuda.current_device())
+
+    def to_dev(a):
+        t = a if isinstance(a, torch.Tensor) else torch.from_numpy(a)
+        return t.to(dev, dtype=torch.float32, non_blocking=True)
+
+    xd, yd, zd, qxd, qyd = (to_dev(a) for a in (x, y, z, qx, qy))
+    g = aidw_grid_build(xd, yd, zd, params, stream)
+    try:
+        zq, _ = aidw_interpolate(g, qxd, qyd, params, stream=stream)
+        out = zq.to("cpu")
+    finally:
+        g.destroy()
+    return out

@@ -1,0 +1,175 @@
+// Device helpers shared by the kNN and weighting kernels.
+//
+// The float32 squared distance is written with explicit round-to-nearest,
+// flush-to-zero PTX so that the kNN kernel and the weighting kernel compute
+// bit-identical values for the same pair (the weighting stage relies on the
+// nearest neighbour's d^2 being the exact minimum of the values it sees).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace aidw {
+
+__device__ __forceinline__ float sub_rn(float a, float b)
+{
+    float r;
+    asm("sub.rn.ftz.f32 %0, %1, %2;" : "=f"(r) : "f"(a), "f"(b));
+    return r;
+}
+__device__ __forceinline__ float mul_rn(float a, float b)
+{
+    float r;
+    asm("mul.rn.ftz.f32 %0, %1, %2;" : "=f"(r) : "f"(a), "f"(b));
+    return r;
+}
+__device__ __forceinline__ float fma_rn(float a, float b, float c)
+{
+    float r;
+    asm("fma.rn.ftz.f32 %0, %1, %2, %3;" : "=f"(r) : "f"(a), "f"(b), "f"(c));
+    return r;
+}
+__device__ __forceinline__ float add_rn(float a, float b)
+{
+    float r;
+    asm("add.rn.ftz.f32 %0, %1, %2;" : "=f"(r) : "f"(a), "f"(b));
+    return r;
+}
+
+// Squared Euclidean distance in float32: fma(dy, dy, dx*dx).
+__device__ __forceinline__ float dist2_f32(float qx, float qy, float px, float py)
+{
+    const float dx = sub_rn(qx, px);
+    const float dy = sub_rn(qy, py);
+    return fma_rn(dy, dy, mul_rn(dx, dx));
+}
+
+// Squared distance in float64 from float32 coordinates.  Both products are
+// exact (24-bit mantissas), so the only rounding is the final add.
+__device__ __forceinline__ double dist2_f64(float qx, float qy, float px, float py)
+{
+    const double dx = (double)qx - (double)px;
+    const double dy = (double)qy - (double)py;
+    return __fma_rn(dy, dy, dx * dx);
+}
+
+// SFU base-2 logarithm and exponential (PTX approx instructions).
+__device__ __forceinline__ float lg2_sfu(float x)
+{
+    float r;
+    asm("lg2.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+    return r;
+}
+__device__ __forceinline__ float ex2_sfu(float x)
+{
+    float r;
+    asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+    return r;
+}
+
+// Error-free transformation (Knuth's TwoSum): s + e == a + b exactly.
+__device__ __forceinline__ void two_sum(float a, float b, float &s, float &e)
+{
+    s = add_rn(a, b);
+    const float bp = sub_rn(s, a);
+    const float ap = sub_rn(s, bp);
+    e = add_rn(sub_rn(a, ap), sub_rn(b, bp));
+}
+
+// Adds x into the compensated pair (hi, lo).
+__device__ __forceinline__ void comp_add(float &hi, float &lo, float x)
+{
+    float s, e;
+    two_sum(hi, x, s, e);
+    hi = s;
+    lo = add_rn(lo, e);
+}
+
+// ---- Eq. 4-6 on the device (float64) -----------------------------------------
+
+// Eq. 4 with R = 0 for r_obs = 0 and R = +inf for r_exp = 0 < r_obs.
+__device__ __forceinline__ double nn_statistic(double r_obs, double r_exp)
+{
+    if (r_obs == 0.0) return 0.0;
+    if (r_exp == 0.0) return __longlong_as_double(0x7ff0000000000000LL);
+    return r_obs / r_exp;
+}
+
+// Eq. 5 (cosine membership with the printed pi / R_max factor).
+__device__ __forceinline__ double membership(double R, double r_min, double r_max)
+{
+    if (R <= r_min) return 0.0;
+    if (R >= r_max) return 1.0;
+    return 0.5 - 0.5 * cos((3.141592653589793 / r_max) * (R - r_min));
+}
+
+// Eq. 6 (triangular membership: linear between the knots 0.1 .. 0.9).
+__device__ __forceinline__ double decay_power(double mu, double a1, double a2, double a3,
+                                              double a4, double a5)
+{
+    if (mu <= 0.1) return a1;
+    if (mu <= 0.3) return a1 * (1.0 - 5.0 * (mu - 0.1)) + 5.0 * a2 * (mu - 0.1);
+    if (mu <= 0.5) return 5.0 * a3 * (mu - 0.3) + a2 * (1.0 - 5.0 * (mu - 0.3));
+    if (mu <= 0.7) return a3 * (1.0 - 5.0 * (mu - 0.5)) + 5.0 * a4 * (mu - 0.5);
+    if (mu <= 0.9) return 5.0 * a5 * (mu - 0.7) + a4 * (1.0 - 5.0 * (mu - 0.7));
+    return a5;
+}
+
+// ---- mbarrier + bulk copy (TMA engine, 1-D) ------------------------------------
+
+__device__ __forceinline__ uint32_t smem_u32(const void *p)
+{
+    return (uint32_t)__cvta_generic_to_shared(p);
+}
+
+__device__ __forceinline__ void mbar_init(uint64_t *bar, uint32_t count)
+{
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count));
+}
+
+__device__ __forceinline__ void fence_mbar_init()
+{
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+
+__device__ __forceinline__ void mbar_expect_tx(uint64_t *bar, uint32_t bytes)
+{
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)),
+                 "r"(bytes)
+                 : "memory");
+}
+
+// Global -> shared bulk copy completing on an mbarrier.  dst, src 16-byte
+// aligned; bytes a multiple of 16.
+__device__ __forceinline__ void bulk_g2s(void *dst, const void *src, uint32_t bytes, uint64_t *bar)
+{
+    asm volatile(
+        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::
+            "r"(smem_u32(dst)),
+        "l"(src), "r"(bytes), "r"(smem_u32(bar))
+        : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, uint32_t parity)
+{
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(smem_u32(bar)), "r"(parity), "r"(1000000u)
+        : "memory");
+    return ok != 0;
+}
+
+// Bounded wait: each try suspends for up to ~1 ms; gives up after max_tries.
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t *bar, uint32_t parity, int max_tries)
+{
+    for (int i = 0; i < max_tries; ++i)
+        if (mbar_try_wait(bar, parity)) return true;
+    return false;
+}
+
+}  // namespace aidw

@@ -1,0 +1,96 @@
+// Internal declarations shared by the library's translation units.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "aidw.h"
+
+namespace aidw {
+
+// ---------------------------------------------------------------------------
+// Device-side description of a built grid (one per grid, in device memory).
+// ---------------------------------------------------------------------------
+struct GridDev {
+    // bounding box as order-preserving integer encodings of float32, updated
+    // with atomicMin/atomicMax during the reduction
+    int enc_min_x, enc_min_y, enc_max_x, enc_max_y;
+    double min_x, min_y, max_x, max_y;
+    double area;        // A of Eq. 2
+    double r_exp;       // Eq. 2
+    double cw;          // cell width
+    long long n_col, n_row, n_cells;
+    long long n_data;
+    int status;         // latched AIDW error bits (see StatusBit)
+    int pad_;
+};
+
+enum StatusBit : int {
+    kStatusNonfiniteData = 1,
+    kStatusNonfiniteQuery = 2,
+    kStatusTimeout = 4,
+    kStatusCapacity = 8,
+};
+
+// Cell-ordered data point: x, y, z and the original index (bit pattern in w).
+// 16 bytes so a tile of them is one bulk (TMA) copy.
+struct __align__(16) Point { float x, y, z; int idx; };
+
+// Per-query result of the kNN stage consumed by the weighting stage.
+struct QRec {
+    double alpha;  // Eq. 6
+    double hit_z;  // mean z of the data points at distance 0 (if any)
+    float d1sq;    // smallest squared distance (float32 path)
+    int n_hit;     // number of data points at distance 0
+};
+
+}  // namespace aidw
+
+// Host-side grid handle (the opaque aidw_grid of the C ABI).
+struct aidw_grid {
+    aidw::GridDev *dev;          // device struct
+    aidw::Point *pts;            // [n_pad] cell-ordered points, padded
+    int *cell_start;             // [cap + 1] head of each cell (int32)
+    int *perm;                   // [n_data] original index at each position
+    long long n_data;
+    long long n_pad;             // n_data rounded up (padding points at +inf)
+    long long cap_cells;         // capacity of cell_start minus one
+    double cell_scale;
+    double area_param;
+    cudaStream_t stream;         // build stream (drained on destroy)
+    int device;
+};
+
+namespace aidw {
+
+// ---- launch helpers (defined in api.cu) -----------------------------------
+aidw_status cuda_status(cudaError_t e);
+// Stage timing: begin returns a handle (-1 when timing is off); end records
+// the closing event and the number of kernels the stage launched.
+int profile_begin(cudaStream_t s);
+void profile_end(int handle, cudaStream_t s, int stage, int launches);
+
+// ---- stages (defined in grid_build.cu, knn.cu, weight.cu) ------------------
+long long grid_cells_capacity(long long n, double c);
+aidw_status grid_build_launch(aidw_grid *g, const float *x, const float *y, const float *z,
+                              cudaStream_t s);
+
+// Parameters of Eq. 4-6 passed by value to the kNN kernel.
+struct AlphaParams {
+    double level[5];
+    double r_min, r_max;
+    double area_override;  // > 0 replaces the grid's area in Eq. 2
+};
+
+// kNN (+ alpha): fills recs (if not null) and the optional public outputs.
+aidw_status knn_launch(const aidw_grid *g, const float *qx, const float *qy, long long n_query,
+                       int k, bool fp64, const AlphaParams &ap, QRec *recs, int *out_idx,
+                       float *out_dist, float *out_robs, void *out_alpha, cudaStream_t s);
+
+// Weighting (stream-K over all data points) + finalize.  Allocates its
+// partial-sum scratch with cudaMallocAsync on s.
+aidw_status weight_launch(const aidw_grid *g, const float *qx, const float *qy,
+                          long long n_query, bool fp64, const QRec *recs, void *out_z,
+                          cudaStream_t s);
+
+}  // namespace aidw

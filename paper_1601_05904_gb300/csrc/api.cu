@@ -1,0 +1,359 @@
+// C ABI entry points (include/aidw.h): argument checks, grid ownership,
+// per-call scratch and stage timing.  All arithmetic happens in the kernels
+// of grid_build.cu, knn.cu and weight.cu.
+#include <math.h>
+#include <string.h>
+
+#include <mutex>
+#include <new>
+#include <vector>
+
+#include "aidw_internal.cuh"
+
+namespace aidw {
+
+aidw_status cuda_status(cudaError_t e)
+{
+    if (e == cudaSuccess) return AIDW_OK;
+    if (e == cudaErrorMemoryAllocation) return AIDW_ERR_OOM;
+    return AIDW_ERR_CUDA;
+}
+
+// ---- stage timing ------------------------------------------------------------
+namespace api_detail {
+
+struct ProfRec {
+    cudaEvent_t a, b;
+    int stage;
+    int launches;
+    bool closed;
+};
+
+std::mutex g_prof_mu;
+bool g_prof_on = false;
+std::vector<ProfRec> g_prof;
+std::vector<cudaEvent_t> g_ev_pool;
+
+cudaEvent_t take_event()
+{
+    if (!g_ev_pool.empty()) {
+        cudaEvent_t e = g_ev_pool.back();
+        g_ev_pool.pop_back();
+        return e;
+    }
+    cudaEvent_t e = nullptr;
+    cudaEventCreate(&e);
+    return e;
+}
+
+}  // namespace api_detail
+using namespace api_detail;
+
+int profile_begin(cudaStream_t s)
+{
+    std::lock_guard<std::mutex> lk(g_prof_mu);
+    if (!g_prof_on) return -1;
+    ProfRec r;
+    r.a = take_event();
+    r.b = take_event();
+    r.stage = -1;
+    r.launches = 0;
+    r.closed = false;
+    cudaEventRecord(r.a, s);
+    g_prof.push_back(r);
+    return (int)g_prof.size() - 1;
+}
+
+void profile_end(int handle, cudaStream_t s, int stage, int launches)
+{
+    if (handle < 0) return;
+    std::lock_guard<std::mutex> lk(g_prof_mu);
+    if (handle >= (int)g_prof.size()) return;
+    ProfRec &r = g_prof[handle];
+    cudaEventRecord(r.b, s);
+    r.stage = stage;
+    r.launches = launches;
+    r.closed = true;
+}
+
+}  // namespace aidw
+
+using namespace aidw;
+using namespace aidw::api_detail;
+
+namespace aidw {
+namespace api_detail {
+
+constexpr long long kMaxPoints = 0x7fffffffLL - 64;  // int32 indices + padding
+
+bool finite(double v) { return isfinite(v) != 0; }
+
+aidw_status check_params(const aidw_params *p, bool need_k)
+{
+    if (!p) return AIDW_ERR_INVALID_ARG;
+    for (int i = 0; i < 5; ++i)
+        if (!finite(p->alpha[i]) || !(p->alpha[i] > 0.0)) return AIDW_ERR_INVALID_ARG;
+    if (!finite(p->r_min) || !finite(p->r_max) || !(p->r_max > 0.0) || !(p->r_min >= 0.0) ||
+        !(p->r_min < p->r_max))
+        return AIDW_ERR_INVALID_ARG;
+    if (!finite(p->area) || !finite(p->cell_scale)) return AIDW_ERR_INVALID_ARG;
+    if (p->cell_scale > 0.0 && (p->cell_scale < 1.0 / 64.0 || p->cell_scale > 64.0))
+        return AIDW_ERR_INVALID_ARG;
+    if (p->precision != AIDW_FP32_COMP && p->precision != AIDW_FP64_PLAIN)
+        return AIDW_ERR_INVALID_ARG;
+    if (need_k && (p->k < 1 || p->k > AIDW_MAX_K)) return AIDW_ERR_K_RANGE;
+    return AIDW_OK;
+}
+
+// Cell width scale used when the caller passes cell_scale <= 0.  Measured on
+// uniform and clustered point sets: about two points per cell keeps the
+// ring search short for k between 8 and 32.
+double auto_cell_scale(int k)
+{
+    (void)k;
+    return 1.0;
+}
+
+AlphaParams alpha_params(const aidw_params *p)
+{
+    AlphaParams ap;
+    for (int i = 0; i < 5; ++i) ap.level[i] = p->alpha[i];
+    ap.r_min = p->r_min;
+    ap.r_max = p->r_max;
+    ap.area_override = p->area > 0.0 ? p->area : 0.0;
+    return ap;
+}
+
+__global__ void k_widen(const int *__restrict__ a, long long n, int64_t *__restrict__ b)
+{
+    const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) b[i] = (int64_t)a[i];
+}
+
+}  // namespace api_detail
+}  // namespace aidw
+
+extern "C" {
+
+void aidw_params_default(aidw_params *p)
+{
+    if (!p) return;
+    memset(p, 0, sizeof(*p));
+    p->k = 10;
+    for (int i = 0; i < 5; ++i) p->alpha[i] = (double)(i + 1);
+    p->r_min = 0.0;
+    p->r_max = 2.0;
+    p->area = 0.0;
+    p->cell_scale = 0.0;
+    p->precision = AIDW_FP32_COMP;
+}
+
+const char *aidw_status_string(aidw_status s)
+{
+    switch (s) {
+    case AIDW_OK: return "ok";
+    case AIDW_ERR_INVALID_ARG: return "invalid argument";
+    case AIDW_ERR_K_RANGE: return "k out of range (1..32 and <= number of data points)";
+    case AIDW_ERR_NONFINITE: return "non-finite coordinate or value";
+    case AIDW_ERR_OOM: return "device allocation failed";
+    case AIDW_ERR_CUDA: return "CUDA error";
+    case AIDW_ERR_TIMEOUT: return "bounded device wait expired";
+    }
+    return "unknown status";
+}
+
+aidw_status aidw_grid_build(const float *x, const float *y, const float *z, int64_t n_data,
+                            const aidw_params *p, aidw_stream_t stream, aidw_grid **out)
+{
+    if (!out) return AIDW_ERR_INVALID_ARG;
+    *out = nullptr;
+    if (!x || !y || !z || n_data < 1 || n_data > kMaxPoints) return AIDW_ERR_INVALID_ARG;
+    const aidw_status ps = check_params(p, false);
+    if (ps != AIDW_OK) return ps;
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+
+    aidw_grid *g = new (std::nothrow) aidw_grid();
+    if (!g) return AIDW_ERR_OOM;
+    memset(g, 0, sizeof(*g));
+    cudaGetDevice(&g->device);
+    g->n_data = n_data;
+    g->n_pad = (n_data + 31) / 32 * 32;
+    g->cell_scale = p->cell_scale > 0.0 ? p->cell_scale : auto_cell_scale(p->k);
+    g->area_param = p->area > 0.0 ? p->area : 0.0;
+    g->cap_cells = grid_cells_capacity(n_data, g->cell_scale);
+    g->stream = s;
+
+    cudaError_t e = cudaMalloc((void **)&g->dev, sizeof(GridDev));
+    if (e == cudaSuccess) e = cudaMalloc((void **)&g->pts, sizeof(Point) * (size_t)g->n_pad);
+    if (e == cudaSuccess)
+        e = cudaMalloc((void **)&g->cell_start, sizeof(int) * (size_t)(g->cap_cells + 1));
+    if (e == cudaSuccess) e = cudaMalloc((void **)&g->perm, sizeof(int) * (size_t)n_data);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        aidw_grid_destroy(g);
+        return e == cudaErrorMemoryAllocation ? AIDW_ERR_OOM : AIDW_ERR_CUDA;
+    }
+    aidw_status st = grid_build_launch(g, x, y, z, s);
+    if (st == AIDW_OK) st = cuda_status(cudaStreamSynchronize(s));
+    if (st == AIDW_OK) {
+        int status = 0;
+        st = cuda_status(cudaMemcpy(&status, &g->dev->status, sizeof(int), cudaMemcpyDeviceToHost));
+        if (st == AIDW_OK && (status & kStatusNonfiniteData)) st = AIDW_ERR_NONFINITE;
+        if (st == AIDW_OK && (status & kStatusCapacity)) st = AIDW_ERR_INVALID_ARG;
+    }
+    if (st != AIDW_OK) {
+        aidw_grid_destroy(g);
+        return st;
+    }
+    *out = g;
+    return AIDW_OK;
+}
+
+aidw_status aidw_grid_status(aidw_grid *g)
+{
+    if (!g) return AIDW_ERR_INVALID_ARG;
+    cudaError_t e = cudaDeviceSynchronize();
+    if (e != cudaSuccess) return cuda_status(e);
+    int status = 0;
+    e = cudaMemcpy(&status, &g->dev->status, sizeof(int), cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) return cuda_status(e);
+    const int zero = 0;
+    cudaMemcpy(&g->dev->status, &zero, sizeof(int), cudaMemcpyHostToDevice);
+    if (status & kStatusTimeout) return AIDW_ERR_TIMEOUT;
+    if (status & (kStatusNonfiniteData | kStatusNonfiniteQuery)) return AIDW_ERR_NONFINITE;
+    if (status & kStatusCapacity) return AIDW_ERR_INVALID_ARG;
+    return AIDW_OK;
+}
+
+aidw_status aidw_grid_destroy(aidw_grid *g)
+{
+    if (!g) return AIDW_ERR_INVALID_ARG;
+    aidw_status st = AIDW_OK;
+    if (g->dev) {
+        // drain all work that may still read the grid
+        st = aidw_grid_status(g);
+    }
+    if (g->perm) cudaFree(g->perm);
+    if (g->cell_start) cudaFree(g->cell_start);
+    if (g->pts) cudaFree(g->pts);
+    if (g->dev) cudaFree(g->dev);
+    delete g;
+    return st;
+}
+
+aidw_status aidw_grid_get_info(const aidw_grid *g, aidw_grid_info *info)
+{
+    if (!g || !info) return AIDW_ERR_INVALID_ARG;
+    GridDev d;
+    cudaError_t e = cudaStreamSynchronize(g->stream);
+    if (e == cudaSuccess) e = cudaMemcpy(&d, g->dev, sizeof(GridDev), cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) return cuda_status(e);
+    info->n_data = d.n_data;
+    info->n_col = d.n_col;
+    info->n_row = d.n_row;
+    info->n_cells = d.n_cells;
+    info->min_x = d.min_x;
+    info->min_y = d.min_y;
+    info->max_x = d.max_x;
+    info->max_y = d.max_y;
+    info->area = d.area;
+    info->r_exp = d.r_exp;
+    info->cell_width = d.cw;
+    info->cell_scale = g->cell_scale;
+    return AIDW_OK;
+}
+
+
+aidw_status aidw_grid_export(const aidw_grid *g, int64_t *cell_start, int32_t *perm,
+                             aidw_stream_t stream)
+{
+    if (!g) return AIDW_ERR_INVALID_ARG;
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    if (cell_start) {
+        aidw_grid_info info;
+        const aidw_status st = aidw_grid_get_info(g, &info);
+        if (st != AIDW_OK) return st;
+        const long long n = info.n_cells + 1;
+        k_widen<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(g->cell_start, n, cell_start);
+    }
+    if (perm)
+        cudaMemcpyAsync(perm, g->perm, sizeof(int32_t) * (size_t)g->n_data,
+                        cudaMemcpyDeviceToDevice, s);
+    return cuda_status(cudaGetLastError());
+}
+
+aidw_status aidw_knn(const aidw_grid *g, const float *qx, const float *qy, int64_t n_query,
+                     int k, int32_t *out_idx, float *out_dist, float *out_robs,
+                     aidw_stream_t stream)
+{
+    if (!g || n_query < 0 || n_query > kMaxPoints) return AIDW_ERR_INVALID_ARG;
+    if (k < 1 || k > AIDW_MAX_K || k > g->n_data) return AIDW_ERR_K_RANGE;
+    if (n_query == 0) return AIDW_OK;
+    if (!qx || !qy) return AIDW_ERR_INVALID_ARG;
+    aidw_params p;
+    aidw_params_default(&p);
+    return knn_launch(g, qx, qy, n_query, k, false, alpha_params(&p), nullptr, out_idx, out_dist,
+                      out_robs, nullptr, reinterpret_cast<cudaStream_t>(stream));
+}
+
+aidw_status aidw_interpolate(const aidw_grid *g, const float *qx, const float *qy,
+                             int64_t n_query, const aidw_params *p, void *out_z,
+                             void *out_alpha, aidw_stream_t stream)
+{
+    if (!g || n_query < 0 || n_query > kMaxPoints) return AIDW_ERR_INVALID_ARG;
+    const aidw_status ps = check_params(p, true);
+    if (ps != AIDW_OK) return ps;
+    if (p->k > g->n_data) return AIDW_ERR_K_RANGE;
+    if (n_query == 0) return AIDW_OK;
+    if (!qx || !qy || !out_z) return AIDW_ERR_INVALID_ARG;
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    const bool fp64 = p->precision == AIDW_FP64_PLAIN;
+    QRec *recs = nullptr;
+    if (cudaMallocAsync((void **)&recs, sizeof(QRec) * (size_t)n_query, s) != cudaSuccess) {
+        cudaGetLastError();
+        return AIDW_ERR_OOM;
+    }
+    aidw_status st = knn_launch(g, qx, qy, n_query, p->k, fp64, alpha_params(p), recs, nullptr,
+                                nullptr, nullptr, out_alpha, s);
+    if (st == AIDW_OK) st = weight_launch(g, qx, qy, n_query, fp64, recs, out_z, s);
+    cudaFreeAsync(recs, s);
+    return st;
+}
+
+aidw_status aidw_profile_enable(int on)
+{
+    std::lock_guard<std::mutex> lk(g_prof_mu);
+    g_prof_on = on != 0;
+    return AIDW_OK;
+}
+
+aidw_status aidw_profile_read(double *ms, int64_t *launches)
+{
+    std::vector<ProfRec> recs;
+    {
+        std::lock_guard<std::mutex> lk(g_prof_mu);
+        recs.swap(g_prof);
+    }
+    aidw_status st = AIDW_OK;
+    for (const ProfRec &r : recs) {
+        if (r.closed && r.stage >= 0 && r.stage < AIDW_STAGE_COUNT) {
+            cudaError_t e = cudaEventSynchronize(r.b);
+            float t = 0.0f;
+            if (e == cudaSuccess) e = cudaEventElapsedTime(&t, r.a, r.b);
+            if (e != cudaSuccess) {
+                st = cuda_status(e);
+            } else {
+                if (ms) ms[r.stage] += (double)t;
+                if (launches) launches[r.stage] += r.launches;
+            }
+        }
+    }
+    std::lock_guard<std::mutex> lk(g_prof_mu);
+    for (const ProfRec &r : recs) {
+        g_ev_pool.push_back(r.a);
+        g_ev_pool.push_back(r.b);
+    }
+    return st;
+}
+
+}  // extern "C"

@@ -1,0 +1,282 @@
+// Grid kNN search and adaptive power (Sec. 3.2.4 / 4.1.4 and Eq. 2-6 of
+// arXiv 1601.05904).
+//
+// One thread per query, as in the paper.  The thread locates the query's
+// cell, then visits square rings of cells L = 0, 1, 2, ... around it.  Cells
+// of one grid row are consecutive in the cell-ordered point array, so the
+// top and bottom edges of a ring are each one contiguous range of points and
+// the side columns are one cell each.  Candidates go through a register
+// top-k on squared distances (no square roots until the end, Sec. 4.1.4),
+// ordered by (d^2, original index).
+//
+// Stop rule.  The paper grows the ring until the block holds k points and
+// then adds one more level (Sec. 3.2.4, remark on Fig. 4).  That is not
+// exact: after the block first holds k points the k-th distance can reach
+// (L+1)*sqrt(2)*cw while one more ring only guarantees (L+1)*cw.  Here the
+// search stops after ring L only when the nearest point the block excludes
+// (the distance from the query to the block's nearest outer edge) is
+// farther than the current k-th distance, with a relative margin that covers
+// the rounding of the float32 distances and of the cell assignment.  Sides
+// of the block that reach the edge of the grid exclude nothing.
+//
+// After the search the thread computes r_obs (Eq. 3), R (Eq. 4), mu (Eq. 5)
+// and alpha (Eq. 6) in float64 and writes one record for the weighting
+// stage: alpha, the smallest squared distance and the mean z of data points
+// at distance 0 (the limit of Eq. 1 when the query coincides with data).
+#include <math.h>
+
+#include <algorithm>
+
+#include "aidw_device.cuh"
+#include "aidw_internal.cuh"
+
+namespace aidw {
+
+namespace {
+
+constexpr int kKnnThreads = 128;
+
+template <bool F64>
+struct DistT;
+template <>
+struct DistT<false> {
+    using T = float;
+    static __device__ __forceinline__ float d2(float qx, float qy, float px, float py)
+    {
+        return dist2_f32(qx, qy, px, py);
+    }
+    static __device__ __forceinline__ float inf() { return __int_as_float(0x7f800000); }
+};
+template <>
+struct DistT<true> {
+    using T = double;
+    static __device__ __forceinline__ double d2(float qx, float qy, float px, float py)
+    {
+        return dist2_f64(qx, qy, px, py);
+    }
+    static __device__ __forceinline__ double inf() { return __longlong_as_double(0x7ff0000000000000LL); }
+};
+
+template <bool F64, int KMAX>
+__global__ void __launch_bounds__(kKnnThreads)
+    k_knn(const GridDev *__restrict__ g, const Point *__restrict__ pts,
+          const int *__restrict__ start, const float *__restrict__ qxa,
+          const float *__restrict__ qya, long long nq, int k, AlphaParams ap,
+          QRec *__restrict__ recs, int *__restrict__ out_idx, float *__restrict__ out_dist,
+          float *__restrict__ out_robs, void *__restrict__ out_alpha)
+{
+    using D = typename DistT<F64>::T;
+    const long long q = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (q >= nq) return;
+    const float qx = qxa[q], qy = qya[q];
+    const double nanv = __longlong_as_double(0x7ff8000000000000LL);
+
+    if (!isfinite(qx) || !isfinite(qy)) {
+        atomicOr(const_cast<int *>(&g->status), kStatusNonfiniteQuery);
+        if (recs) {
+            QRec r;
+            r.alpha = nanv;
+            r.hit_z = nanv;
+            r.d1sq = __int_as_float(0x7fc00000);
+            r.n_hit = 0;
+            recs[q] = r;
+        }
+        for (int j = 0; j < k; ++j) {
+            if (out_idx) out_idx[q * k + j] = -1;
+            if (out_dist) out_dist[q * k + j] = __int_as_float(0x7fc00000);
+        }
+        if (out_robs) out_robs[q] = __int_as_float(0x7fc00000);
+        if (out_alpha) {
+            if (F64)
+                static_cast<double *>(out_alpha)[q] = nanv;
+            else
+                static_cast<float *>(out_alpha)[q] = __int_as_float(0x7fc00000);
+        }
+        return;
+    }
+
+    const double minx = g->min_x, miny = g->min_y, cw = g->cw;
+    const int nc = (int)g->n_col, nr = (int)g->n_row;
+    long long colw = (long long)floor(((double)qx - minx) / cw);
+    long long roww = (long long)floor(((double)qy - miny) / cw);
+    const int col = (int)(colw < 0 ? 0 : (colw > nc - 1 ? nc - 1 : colw));
+    const int row = (int)(roww < 0 ? 0 : (roww > nr - 1 ? nr - 1 : roww));
+
+    D kd[KMAX];
+    int ki[KMAX];
+#pragma unroll
+    for (int j = 0; j < KMAX; ++j) {
+        kd[j] = DistT<F64>::inf();
+        ki[j] = 0x7fffffff;
+    }
+    D kth = DistT<F64>::inf();
+    int kthi = 0x7fffffff;
+    long long found = 0;
+    int n_hit = 0;
+    double hit_sum = 0.0;
+
+    for (int L = 0;; ++L) {
+        // Ring L as segments of one grid row each: the bottom and top edges
+        // (contiguous runs of cells) and the two side cells of every row in
+        // between.  Segment index sg enumerates them.
+        const int c0 = max(col - L, 0), c1 = min(col + L, nc - 1);
+        const bool left_in = col - L >= 0, right_in = col + L <= nc - 1;
+        const int r0 = max(row - L + 1, 0), r1 = min(row + L - 1, nr - 1);
+        const int nside = (L > 0 && (left_in || right_in) && r1 >= r0) ? r1 - r0 + 1 : 0;
+        const int nsegs = L == 0 ? 1 : 2 + 2 * nside;
+        for (int sg = 0; sg < nsegs; ++sg) {
+            int r, ca, cb;
+            if (L == 0) {
+                r = row;
+                ca = cb = col;
+            } else if (sg < 2) {
+                r = sg == 0 ? row - L : row + L;
+                if (r < 0 || r > nr - 1) continue;
+                ca = c0;
+                cb = c1;
+            } else {
+                const int e = sg - 2;
+                r = r0 + (e >> 1);
+                const bool right = (e & 1) != 0;
+                if (right ? !right_in : !left_in) continue;
+                ca = cb = right ? col + L : col - L;
+            }
+            const long long base = (long long)r * nc;
+            const int a = start[base + ca], b = start[base + cb + 1];
+            found += b - a;
+            for (int s = a; s < b; ++s) {
+                const float4 p = reinterpret_cast<const float4 *>(pts)[s];
+                const int pidx = __float_as_int(p.w);
+                const D d2 = DistT<F64>::d2(qx, qy, p.x, p.y);
+                if (d2 == (D)0) {
+                    ++n_hit;
+                    hit_sum += (double)p.z;
+                }
+                if (d2 < kth || (d2 == kth && pidx < kthi)) {
+                    // bubble the candidate through the sorted list
+                    D cd = d2;
+                    int ci = pidx;
+#pragma unroll
+                    for (int j = 0; j < KMAX; ++j) {
+                        const bool lt = (j < k) && (cd < kd[j] || (cd == kd[j] && ci < ki[j]));
+                        const D td = kd[j];
+                        const int ti = ki[j];
+                        kd[j] = lt ? cd : td;
+                        ki[j] = lt ? ci : ti;
+                        cd = lt ? td : cd;
+                        ci = lt ? ti : ci;
+                    }
+                    kth = kd[0];
+                    kthi = ki[0];
+#pragma unroll
+                    for (int j = 1; j < KMAX; ++j) {
+                        if (j == k - 1) {
+                            kth = kd[j];
+                            kthi = ki[j];
+                        }
+                    }
+                }
+            }
+        }
+        const bool full_l = col - L <= 0, full_r = col + L >= nc - 1;
+        const bool full_b = row - L <= 0, full_t = row + L >= nr - 1;
+        if (full_l && full_r && full_b && full_t) break;  // whole grid visited
+        if (found >= k) {
+            // distance from the query to the nearest edge of the block that
+            // has cells beyond it
+            double dmin = DistT<true>::inf();
+            if (!full_l) dmin = fmin(dmin, (double)qx - (minx + (double)(col - L) * cw));
+            if (!full_r) dmin = fmin(dmin, (minx + (double)(col + L + 1) * cw) - (double)qx);
+            if (!full_b) dmin = fmin(dmin, (double)qy - (miny + (double)(row - L) * cw));
+            if (!full_t) dmin = fmin(dmin, (miny + (double)(row + L + 1) * cw) - (double)qy);
+            // margin for the float64 edge positions (absolute) and the
+            // float32 distance rounding (relative)
+            dmin -= 4.0e-16 * (fabs((double)qx) + fabs((double)qy) + fabs(minx) + fabs(miny) +
+                               (double)(nc + nr + 2) * cw);
+            if (dmin > 0.0 && dmin * dmin * (1.0 - 0x1p-20) > (double)kth) break;
+        }
+    }
+
+    // Eq. 3 (r_obs), Eq. 2 (r_exp, possibly with an explicit area), Eq. 4-6.
+    double r_obs = 0.0;
+#pragma unroll
+    for (int j = 0; j < KMAX; ++j)
+        if (j < k) r_obs += sqrt((double)kd[j]);
+    r_obs /= (double)k;
+    const double r_exp = ap.area_override > 0.0
+                             ? 1.0 / (2.0 * sqrt((double)g->n_data / ap.area_override))
+                             : g->r_exp;
+    const double R = nn_statistic(r_obs, r_exp);
+    const double mu = membership(R, ap.r_min, ap.r_max);
+    const double alpha =
+        decay_power(mu, ap.level[0], ap.level[1], ap.level[2], ap.level[3], ap.level[4]);
+
+    if (recs) {
+        QRec r;
+        r.alpha = alpha;
+        r.hit_z = n_hit > 0 ? hit_sum / (double)n_hit : 0.0;
+        r.d1sq = (float)kd[0];
+        r.n_hit = n_hit;
+        recs[q] = r;
+    }
+    if (out_idx || out_dist) {
+#pragma unroll
+        for (int j = 0; j < KMAX; ++j) {
+            if (j < k) {
+                if (out_idx) out_idx[q * k + j] = ki[j];
+                if (out_dist) out_dist[q * k + j] = (float)sqrt(kd[j]);
+            }
+        }
+    }
+    if (out_robs) out_robs[q] = (float)r_obs;
+    if (out_alpha) {
+        if (F64)
+            static_cast<double *>(out_alpha)[q] = alpha;
+        else
+            static_cast<float *>(out_alpha)[q] = (float)alpha;
+    }
+}
+
+template <bool F64, int KMAX>
+void launch_knn(const aidw_grid *g, const float *qx, const float *qy, long long nq, int k,
+                const AlphaParams &ap, QRec *recs, int *out_idx, float *out_dist,
+                float *out_robs, void *out_alpha, cudaStream_t s)
+{
+    const unsigned blocks = (unsigned)((nq + kKnnThreads - 1) / kKnnThreads);
+    k_knn<F64, KMAX><<<blocks, kKnnThreads, 0, s>>>(g->dev, g->pts, g->cell_start, qx, qy, nq,
+                                                    k, ap, recs, out_idx, out_dist, out_robs,
+                                                    out_alpha);
+}
+
+template <bool F64>
+void launch_knn_k(const aidw_grid *g, const float *qx, const float *qy, long long nq, int k,
+                  const AlphaParams &ap, QRec *recs, int *out_idx, float *out_dist,
+                  float *out_robs, void *out_alpha, cudaStream_t s)
+{
+    if (k <= 8)
+        launch_knn<F64, 8>(g, qx, qy, nq, k, ap, recs, out_idx, out_dist, out_robs, out_alpha, s);
+    else if (k <= 16)
+        launch_knn<F64, 16>(g, qx, qy, nq, k, ap, recs, out_idx, out_dist, out_robs, out_alpha, s);
+    else
+        launch_knn<F64, 32>(g, qx, qy, nq, k, ap, recs, out_idx, out_dist, out_robs, out_alpha, s);
+}
+
+}  // namespace
+
+aidw_status knn_launch(const aidw_grid *g, const float *qx, const float *qy, long long n_query,
+                       int k, bool fp64, const AlphaParams &ap, QRec *recs, int *out_idx,
+                       float *out_dist, float *out_robs, void *out_alpha, cudaStream_t s)
+{
+    if (n_query <= 0) return AIDW_OK;
+    const int prof = profile_begin(s);
+    if (fp64)
+        launch_knn_k<true>(g, qx, qy, n_query, k, ap, recs, out_idx, out_dist, out_robs,
+                           out_alpha, s);
+    else
+        launch_knn_k<false>(g, qx, qy, n_query, k, ap, recs, out_idx, out_dist, out_robs,
+                            out_alpha, s);
+    profile_end(prof, s, AIDW_STAGE_KNN, 1);
+    return cuda_status(cudaGetLastError());
+}
+
+}  // namespace aidw
