@@ -153,6 +153,35 @@ aidw_status aidw_interpolate(const aidw_grid *g, const float *qx, const float *q
                              int64_t n_query, const aidw_params *p, void *out_z,
                              void *out_alpha, aidw_stream_t stream);
 
+/* ---- interpolation without device allocation ------------------------------
+ * No counterpart in the paper; this is a library service.  Some callers
+ * cannot let a library allocate device memory: an application that reserves
+ * the GPU's memory up front and hands out slices from its own pool, or a
+ * latency-critical loop where cudaMalloc/cudaFree (which may synchronise the
+ * device, or fail under memory pressure halfway through a pipeline) is not
+ * acceptable.  aidw_interpolate_noalloc computes exactly what
+ * aidw_interpolate computes, but keeps its per-call scratch (the per-query
+ * kNN records and the partial sums of the weighting stage) in one
+ * fixed-size array inside the library's device image, so the call performs
+ * no allocation of any kind.  The caller still passes the grid, the queries
+ * and the outputs.
+ *  - n_query must not exceed AIDW_NOALLOC_MAX_QUERIES; larger calls return
+ *    AIDW_ERR_INVALID_ARG and enqueue nothing.
+ *  - The scratch array (AIDW_NOALLOC_SCRATCH_BYTES) lives in every GPU that
+ *    loads the library until the process exits.
+ *  - The first call on a device looks up the array's device address (host
+ *    set-up); make that first call before any stream capture.
+ *  - Every call on a device shares the one array: calls that can overlap on
+ *    the GPU (different streams, no ordering between them) race on it.
+ *    Calls ordered on one stream are safe.  Nothing in the array needs to
+ *    start at zero; each call overwrites what it reads.
+ *  - The grid must belong to the current device. */
+#define AIDW_NOALLOC_MAX_QUERIES 65536
+#define AIDW_NOALLOC_SCRATCH_BYTES (8u << 20)
+aidw_status aidw_interpolate_noalloc(const aidw_grid *g, const float *qx, const float *qy,
+                                     int64_t n_query, const aidw_params *p, void *out_z,
+                                     void *out_alpha, aidw_stream_t stream);
+
 /* Short English name of a status code (static storage). */
 const char *aidw_status_string(aidw_status s);
 

@@ -93,4 +93,18 @@ aidw_status weight_launch(const aidw_grid *g, const float *qx, const float *qy,
                           long long n_query, bool fp64, const QRec *recs, void *out_z,
                           cudaStream_t s);
 
+// Same computation as weight_launch, with the partial sums in caller-given
+// device memory (scratch_bytes long) instead of an allocation; the number of
+// persistent CTAs is reduced if needed so that the partials fit.  Returns
+// AIDW_ERR_INVALID_ARG if not even one CTA's partials fit.
+aidw_status weight_launch_scratch(const aidw_grid *g, const float *qx, const float *qy,
+                                  long long n_query, bool fp64, const QRec *recs, void *out_z,
+                                  void *scratch, size_t scratch_bytes, cudaStream_t s);
+
+namespace api_detail {
+// Argument checks and Eq. 4-6 parameters shared by the entry points (api.cu).
+aidw_status check_params(const aidw_params *p, bool need_k);
+AlphaParams alpha_params(const aidw_params *p);
+}  // namespace api_detail
+
 }  // namespace aidw

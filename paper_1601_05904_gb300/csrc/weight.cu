@@ -403,7 +403,58 @@ aidw_status run(const aidw_grid *g, const float *qx, const float *qy, long long 
     return cuda_status(cudaGetLastError());
 }
 
+template <bool F64>
+aidw_status run_scratch(const aidw_grid *g, const float *qx, const float *qy, long long nq,
+                        const QRec *recs, void *out_z, void *scratch, size_t scratch_bytes,
+                        cudaStream_t s)
+{
+    using C = WCfg<F64>;
+    using Part = typename std::conditional<F64, double2, float4>::type;
+    SKArgs a;
+    a.pts = g->pts;
+    a.n_pad = g->n_pad;
+    a.D = (g->n_pad + kDTile - 1) / kDTile;
+    a.qx = qx;
+    a.qy = qy;
+    a.nq = nq;
+    a.T = (nq + C::kQTile - 1) / C::kQTile;
+    a.U = a.T * a.D;
+    const long long slot_bytes = (long long)sizeof(Part) * C::kQTile;
+    const long long g_fit = (long long)(scratch_bytes / (size_t)slot_bytes) - a.T;
+    if (g_fit < 1) return AIDW_ERR_INVALID_ARG;
+    a.G = std::min<long long>(std::min<long long>(resident_ctas<F64>(g->device), a.U), g_fit);
+    a.recs = recs;
+    a.status = &g->dev->status;
+    Part *part = static_cast<Part *>(scratch);
+    const size_t smem = (size_t)kStages * kDTile * sizeof(Point);
+    int prof = profile_begin(s);
+    if (F64)
+        k_weight_f64<<<(unsigned)a.G, C::kThreads, smem, s>>>(a, reinterpret_cast<double2 *>(part));
+    else
+        k_weight_f32<<<(unsigned)a.G, C::kThreads, smem, s>>>(a, reinterpret_cast<float4 *>(part));
+    profile_end(prof, s, AIDW_STAGE_WEIGHT, 1);
+    prof = profile_begin(s);
+    const unsigned fb = (unsigned)((nq + 255) / 256);
+    if (F64)
+        k_finalize_f64<<<fb, 256, 0, s>>>(reinterpret_cast<double2 *>(part), recs, nq, a.D, a.U,
+                                          a.G, static_cast<double *>(out_z));
+    else
+        k_finalize_f32<<<fb, 256, 0, s>>>(reinterpret_cast<float4 *>(part), recs, nq, a.D, a.U,
+                                          a.G, static_cast<float *>(out_z));
+    profile_end(prof, s, AIDW_STAGE_FINALIZE, 1);
+    return cuda_status(cudaGetLastError());
+}
+
 }  // namespace
+
+aidw_status weight_launch_scratch(const aidw_grid *g, const float *qx, const float *qy,
+                                  long long n_query, bool fp64, const QRec *recs, void *out_z,
+                                  void *scratch, size_t scratch_bytes, cudaStream_t s)
+{
+    if (n_query <= 0) return AIDW_OK;
+    return fp64 ? run_scratch<true>(g, qx, qy, n_query, recs, out_z, scratch, scratch_bytes, s)
+                : run_scratch<false>(g, qx, qy, n_query, recs, out_z, scratch, scratch_bytes, s);
+}
 
 aidw_status weight_launch(const aidw_grid *g, const float *qx, const float *qy,
                           long long n_query, bool fp64, const QRec *recs, void *out_z,
