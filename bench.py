@@ -37,11 +37,6 @@ if ROOT not in sys.path:
 METRIC = "AIDW interpolated points/s at n=m=1M (kNN+weighting), FP32-comp vs FP64 plain"
 UNIT = "points/s"
 L2_FLUSH_BYTES = 256 << 20
-# SFU (XU pipe) results per SM per clock on GB300.  Derived from ncu: the
-# weighting kernel issues 18 lg2/ex2 per SM per clock and ncu reports the XU
-# pipe at 56.5 % of its peak, i.e. a peak of 32 per SM per clock.
-MUFU_PER_SM_CLK = 32
-MUFU_PER_PAIR = 2         # one lg2 and one ex2 per (query, data point) pair
 
 
 def parse():
@@ -324,13 +319,20 @@ def run_ours(args):
     w_ms, w_launches = stage["weight"]
     pairs = float(w.n) * float(w.m)
     achieved = pairs / (w_ms / w_launches / 1000.0) / 1e9 if w_launches else None
-    peak = MUFU_PER_SM_CLK * props.multi_processor_count * sm_max * 1e6 / MUFU_PER_PAIR / 1e9
+    # Every (query, data point) pair needs one SFU log2 and one SFU exp2; the
+    # two share the SFU pipe, so the pipe bounds the pair rate at
+    # 1 / (1/r_lg2 + 1/r_ex2) per SM per clock (rates measured live).
+    rates = binding.aidw_probe_pipe_rates()
+    pairs_per_sm_clk = 1.0 / (1.0 / rates["lg2"] + 1.0 / rates["ex2"])
+    peak = pairs_per_sm_clk * props.multi_processor_count * sm_max * 1e6 / 1e9
     roofline = {"bound": "alu", "kernel": "k_weight_f32 (all-points weighting, Eq. 1)",
                 "achieved": achieved, "peak": peak, "unit": "Gpair/s",
                 "frac": (achieved / peak) if achieved else None, "traffic": None,
-                "peak_basis": f"SFU issue: {MUFU_PER_SM_CLK} lg2/ex2 per SM per clock x "
-                              f"{props.multi_processor_count} SMs x {sm_max:.0f} MHz max clock / "
-                              f"{MUFU_PER_PAIR} SFU ops per pair"}
+                "peak_basis": (f"SFU pipe: measured lg2 {rates['lg2']:.2f} and ex2 "
+                               f"{rates['ex2']:.2f} per SM per clock -> "
+                               f"{pairs_per_sm_clk:.2f} pairs per SM per clock x "
+                               f"{props.multi_processor_count} SMs x {sm_max:.0f} MHz max clock"),
+                "pipe_rates_per_sm_clk": rates}
     stages_ms = {k: v[0] / args.steps for k, v in stage.items()}
     cpu = None
     if not args.no_cpu_baseline and world >= 1:

@@ -201,6 +201,16 @@ typedef enum {
 aidw_status aidw_profile_enable(int on);
 aidw_status aidw_profile_read(double *ms, int64_t *launches);
 
+/* Measures, on the current device, the sustained per-SM per-clock rate of
+ * the three pipes the weighting stage uses: SFU log2 (lg2.approx), SFU exp2
+ * (ex2.approx) and packed float32 FMA (lanes of fma.f32x2).  One CTA per SM
+ * runs independent chains of each instruction for ~1 ms; rates come from
+ * clock64(), so they do not depend on the clock speed.  Synchronous.
+ * Measurement helper with no counterpart in the paper: the benchmark uses it
+ * as the denominator of the weighting kernel's roofline. */
+aidw_status aidw_probe_pipe_rates(double *lg2_per_sm_clk, double *ex2_per_sm_clk,
+                                  double *ffma2_lanes_per_sm_clk);
+
 #ifdef __cplusplus
 }
 #endif

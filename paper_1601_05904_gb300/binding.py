@@ -116,6 +116,8 @@ def load(path: str | None = None):
         lib.aidw_profile_enable.argtypes = [c_int]
         lib.aidw_profile_read.restype = c_int
         lib.aidw_profile_read.argtypes = [P(ctypes.c_double), P(ctypes.c_int64)]
+        lib.aidw_probe_pipe_rates.restype = c_int
+        lib.aidw_probe_pipe_rates.argtypes = [P(ctypes.c_double)] * 3
         _lib = lib
         return lib
 
@@ -270,6 +272,13 @@ def aidw_profile_read() -> dict:
     ln = (ctypes.c_int64 * len(STAGES))()
     _check(load().aidw_profile_read(ms, ln), "aidw_profile_read")
     return {s: (ms[i], int(ln[i])) for i, s in enumerate(STAGES)}
+
+
+def aidw_probe_pipe_rates() -> dict:
+    """Per-SM per-clock rates of SFU lg2, SFU ex2 and packed FMA lanes."""
+    r = [ctypes.c_double() for _ in range(3)]
+    _check(load().aidw_probe_pipe_rates(*(ctypes.byref(v) for v in r)), "aidw_probe_pipe_rates")
+    return {"lg2": r[0].value, "ex2": r[1].value, "ffma2_lanes": r[2].value}
 
 
 def interpolate_host(x, y, z, qx, qy, params: Params | None = None, stream=None):

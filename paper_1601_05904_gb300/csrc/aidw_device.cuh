@@ -67,6 +67,59 @@ __device__ __forceinline__ float ex2_sfu(float x)
     return r;
 }
 
+// ---- packed float32 pairs (Blackwell f32x2 instructions) ------------------------
+// Two float32 lanes in one 64-bit register pair; lane 0 is the low half.  The
+// packed add/mul/fma round each lane exactly like the scalar .rn.ftz forms
+// above, so a lane of dist2 computed here equals dist2_f32 bit for bit.
+struct F2 {
+    unsigned long long v;
+};
+
+__device__ __forceinline__ F2 f2_pack(float lo, float hi)
+{
+    F2 r;
+    asm("mov.b64 %0, {%1, %2};" : "=l"(r.v) : "f"(lo), "f"(hi));
+    return r;
+}
+__device__ __forceinline__ void f2_unpack(F2 a, float &lo, float &hi)
+{
+    asm("mov.b64 {%0, %1}, %2;" : "=f"(lo), "=f"(hi) : "l"(a.v));
+}
+__device__ __forceinline__ F2 f2_add(F2 a, F2 b)
+{
+    F2 r;
+    asm("add.rn.ftz.f32x2 %0, %1, %2;" : "=l"(r.v) : "l"(a.v), "l"(b.v));
+    return r;
+}
+__device__ __forceinline__ F2 f2_sub(F2 a, F2 b)
+{
+    F2 r;
+    asm("sub.rn.ftz.f32x2 %0, %1, %2;" : "=l"(r.v) : "l"(a.v), "l"(b.v));
+    return r;
+}
+__device__ __forceinline__ F2 f2_mul(F2 a, F2 b)
+{
+    F2 r;
+    asm("mul.rn.ftz.f32x2 %0, %1, %2;" : "=l"(r.v) : "l"(a.v), "l"(b.v));
+    return r;
+}
+__device__ __forceinline__ F2 f2_fma(F2 a, F2 b, F2 c)
+{
+    F2 r;
+    asm("fma.rn.ftz.f32x2 %0, %1, %2, %3;" : "=l"(r.v) : "l"(a.v), "l"(b.v), "l"(c.v));
+    return r;
+}
+// Lane-wise compensated accumulation of x into (hi, lo) with TwoSum.
+__device__ __forceinline__ void f2_comp_add(F2 &hi, F2 &lo, F2 x)
+{
+    const F2 s = f2_add(hi, x);
+    const F2 bp = f2_sub(s, hi);
+    const F2 ap = f2_sub(s, bp);
+    const F2 e = f2_add(f2_sub(hi, ap), f2_sub(x, bp));
+    hi = s;
+    lo = f2_add(lo, e);
+}
+
 // Error-free transformation (Knuth's TwoSum): s + e == a + b exactly.
 __device__ __forceinline__ void two_sum(float a, float b, float &s, float &e)
 {

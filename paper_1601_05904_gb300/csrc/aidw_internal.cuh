@@ -36,6 +36,12 @@ enum StatusBit : int {
 // 16 bytes so a tile of them is one bulk (TMA) copy.
 struct __align__(16) Point { float x, y, z; int idx; };
 
+// Points per tile of the weighting layout: the grid also stores its points
+// as tiles of kWeightTile {-x[], -y[], z[]} float32 arrays (structure of
+// arrays inside a tile, negated coordinates so that q + (-p) == q - p), which
+// the weighting kernel streams into shared memory one tile per bulk copy.
+constexpr int kWeightTile = 1024;
+
 // Per-query result of the kNN stage consumed by the weighting stage.
 struct QRec {
     double alpha;  // Eq. 6
@@ -52,6 +58,8 @@ struct aidw_grid {
     aidw::Point *pts;            // [n_pad] cell-ordered points, padded
     int *cell_start;             // [cap + 1] head of each cell (int32)
     int *perm;                   // [n_data] original index at each position
+    float *wt;                   // [n_wtiles][3][kWeightTile] weighting tiles
+    long long n_wtiles;          // ceil(n_data / kWeightTile)
     long long n_data;
     long long n_pad;             // n_data rounded up (padding points at +inf)
     long long cap_cells;         // capacity of cell_start minus one

@@ -188,6 +188,9 @@ aidw_status aidw_grid_build(const float *x, const float *y, const float *z, int6
     if (e == cudaSuccess)
         e = cudaMalloc((void **)&g->cell_start, sizeof(int) * (size_t)(g->cap_cells + 1));
     if (e == cudaSuccess) e = cudaMalloc((void **)&g->perm, sizeof(int) * (size_t)n_data);
+    g->n_wtiles = (n_data + kWeightTile - 1) / kWeightTile;
+    if (e == cudaSuccess)
+        e = cudaMalloc((void **)&g->wt, sizeof(float) * 3 * kWeightTile * (size_t)g->n_wtiles);
     if (e != cudaSuccess) {
         cudaGetLastError();
         aidw_grid_destroy(g);
@@ -233,6 +236,7 @@ aidw_status aidw_grid_destroy(aidw_grid *g)
         // drain all work that may still read the grid
         st = aidw_grid_status(g);
     }
+    if (g->wt) cudaFree(g->wt);
     if (g->perm) cudaFree(g->perm);
     if (g->cell_start) cudaFree(g->cell_start);
     if (g->pts) cudaFree(g->pts);

@@ -271,7 +271,8 @@ __global__ void __launch_bounds__(kThreads) k_fixup(const float *__restrict__ x,
                                                     const int *__restrict__ start,
                                                     const int *__restrict__ key,
                                                     const int *__restrict__ tmp,
-                                                    Point *__restrict__ pts, int *__restrict__ perm)
+                                                    Point *__restrict__ pts, int *__restrict__ perm,
+                                                    float *__restrict__ wt)
 {
     const long long s = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (s >= n || (g->status & (kStatusNonfiniteData | kStatusCapacity))) return;
@@ -287,18 +288,33 @@ __global__ void __launch_bounds__(kThreads) k_fixup(const float *__restrict__ x,
     p.idx = i;
     pts[a + r] = p;
     perm[a + r] = i;
+    const long long pos = a + r;
+    float *tile = wt + (pos / kWeightTile) * (3 * kWeightTile) + pos % kWeightTile;
+    tile[0] = -p.x;
+    tile[kWeightTile] = -p.y;
+    tile[2 * kWeightTile] = p.z;
 }
 
-__global__ void k_pad(Point *pts, long long n, long long n_pad)
+// Padding after the last point: +inf coordinates, whose weight is exactly 0
+// (d^2 = inf, log2 = inf, exp2(-inf) = 0), in both layouts.
+__global__ void k_pad(Point *pts, long long n, long long n_pad, float *wt, long long n_wpad)
 {
     const long long i = n + (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= n_pad) return;
-    Point p;
-    p.x = __int_as_float(0x7f800000);
-    p.y = __int_as_float(0x7f800000);
-    p.z = 0.0f;
-    p.idx = -1;
-    pts[i] = p;
+    const float inf = __int_as_float(0x7f800000);
+    if (i < n_pad) {
+        Point p;
+        p.x = inf;
+        p.y = inf;
+        p.z = 0.0f;
+        p.idx = -1;
+        pts[i] = p;
+    }
+    if (i < n_wpad) {
+        float *tile = wt + (i / kWeightTile) * (3 * kWeightTile) + i % kWeightTile;
+        tile[0] = -inf;
+        tile[kWeightTile] = -inf;
+        tile[2 * kWeightTile] = 0.0f;
+    }
 }
 
 inline unsigned blocks_for(long long n, int t) { return (unsigned)((n + t - 1) / t); }
@@ -354,10 +370,13 @@ aidw_status grid_build_launch(aidw_grid *g, const float *x, const float *y, cons
     nl += 3;
     k_scatter<<<blocks_for(n, kThreads), kThreads, 0, s>>>(n, g->dev, start, key, rank, tmp);
     k_fixup<<<blocks_for(n, kThreads), kThreads, 0, s>>>(x, y, z, n, g->dev, start, key, tmp,
-                                                         g->pts, g->perm);
+                                                         g->pts, g->perm, g->wt);
     nl += 2;
-    if (g->n_pad > n) {
-        k_pad<<<blocks_for(g->n_pad - n, kThreads), kThreads, 0, s>>>(g->pts, n, g->n_pad);
+    const long long n_wpad = g->n_wtiles * kWeightTile;
+    const long long pad_hi = std::max(g->n_pad, n_wpad);
+    if (pad_hi > n) {
+        k_pad<<<blocks_for(pad_hi - n, kThreads), kThreads, 0, s>>>(g->pts, n, g->n_pad, g->wt,
+                                                                    n_wpad);
         ++nl;
     }
     cudaFreeAsync(key, s);

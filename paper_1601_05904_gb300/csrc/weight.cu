@@ -41,7 +41,8 @@ namespace aidw {
 
 namespace {
 
-constexpr int kDTile = 1024;   // points per shared-memory stage (16 KiB)
+constexpr int kDTile = 1024;   // points per shared-memory stage
+static_assert(kDTile == kWeightTile, "weighting tiles are staged whole");
 constexpr int kStages = 3;
 constexpr int kChunk = 32;     // points per plain float32 partial sum
 constexpr int kWaitTries = 4000;
@@ -75,7 +76,9 @@ __host__ __device__ __forceinline__ long long sk_owner(long long u, long long U,
 }
 
 struct SKArgs {
-    const Point *pts;
+    const Point *pts;  // AoS points (float64 path)
+    const float *wt;   // weighting tiles {-x[], -y[], z[]} (float32 path)
+    long long n_data;
     long long n_pad;   // points incl. padding (multiple of 32)
     long long D;       // data tiles
     const float *qx, *qy;
@@ -99,12 +102,39 @@ __device__ __forceinline__ void issue_tile(const SKArgs &a, Point *buf, uint64_t
 // ---------------------------------------------------------------------------
 // float32 compensated weighting
 // ---------------------------------------------------------------------------
+constexpr int kChunk2 = 2 * kChunk;   // points per plain sum; each lane sums kChunk
+
+// Points of tile d that the float32 kernel processes: the valid ones rounded
+// up to kChunk2 (the tile's padding has weight 0).
+__device__ __forceinline__ int soa_count(const SKArgs &a, long long d)
+{
+    const long long rem = a.n_data - d * kDTile;
+    const long long c = (rem + kChunk2 - 1) / kChunk2 * kChunk2;
+    return (int)min((long long)kDTile, c);
+}
+
+__device__ __forceinline__ void issue_tile_soa(const SKArgs &a, float *buf, uint64_t *bar,
+                                               long long u)
+{
+    const long long d = u % a.D;
+    const uint32_t bytes = (uint32_t)soa_count(a, d) * 4u;
+    const float *src = a.wt + d * (3 * kDTile);
+    mbar_expect_tx(bar, 3u * bytes);
+    bulk_g2s(buf, src, bytes, bar);
+    bulk_g2s(buf + kDTile, src + kDTile, bytes, bar);
+    bulk_g2s(buf + 2 * kDTile, src + 2 * kDTile, bytes, bar);
+}
+
+// Each thread holds kQPT queries; every packed instruction applies one query
+// to two consecutive data points (lanes), so a 16-byte shared load of the
+// tile's x (or y, z) array feeds two packed operands.
 __global__ void __launch_bounds__(WCfg<false>::kThreads, WCfg<false>::kMinBlocks)
     k_weight_f32(SKArgs a, float4 *__restrict__ part)
 {
     using C = WCfg<false>;
+    constexpr int Q = C::kQPT;
     extern __shared__ __align__(128) unsigned char smem_raw[];
-    Point *buf = reinterpret_cast<Point *>(smem_raw);
+    float *buf = reinterpret_cast<float *>(smem_raw);
     __shared__ __align__(8) uint64_t full[kStages];
 
     const long long j = blockIdx.x;
@@ -117,62 +147,80 @@ __global__ void __launch_bounds__(WCfg<false>::kThreads, WCfg<false>::kMinBlocks
     __syncthreads();
     if (threadIdx.x == 0)
         for (int s = 0; s < kStages; ++s)
-            if (u0 + s < u1) issue_tile(a, buf + s * kDTile, &full[s], u0 + s);
+            if (u0 + s < u1) issue_tile_soa(a, buf + s * 3 * kDTile, &full[s], u0 + s);
 
+    const F2 zero2 = f2_pack(0.0f, 0.0f);
     long long u = u0;
     while (u < u1) {
         const long long t = u / a.D;
         const long long seg_end = min(u1, (t + 1) * a.D);
 
-        float qx[C::kQPT], qy[C::kQPT], cq[C::kQPT], bq[C::kQPT];
-        float hw[C::kQPT], lw[C::kQPT], hz[C::kQPT], lz[C::kQPT];
+        F2 qx2[Q], qy2[Q], c2[Q], b2[Q], hw[Q], lw[Q], hz[Q], lz[Q];
 #pragma unroll
-        for (int i = 0; i < C::kQPT; ++i) {
+        for (int i = 0; i < Q; ++i) {
             const long long q = t * C::kQTile + (long long)i * C::kThreads + threadIdx.x;
-            qx[i] = 0.0f;
-            qy[i] = 0.0f;
-            cq[i] = -1.0f;
-            bq[i] = 0.0f;
+            float qx = 0.0f, qy = 0.0f, c = -1.0f, b = 0.0f;
             if (q < a.nq) {
-                qx[i] = a.qx[q];
-                qy[i] = a.qy[q];
+                qx = a.qx[q];
+                qy = a.qy[q];
                 const QRec r = a.recs[q];
                 if (r.n_hit > 0 || !(r.alpha == r.alpha)) {
-                    cq[i] = 0.0f;  // result replaced in the finalize step
+                    c = 0.0f;  // result replaced in the finalize step
                 } else {
-                    cq[i] = (float)(-0.5 * r.alpha);
-                    bq[i] = -cq[i] * lg2_sfu(r.d1sq);
+                    c = (float)(-0.5 * r.alpha);
+                    b = -c * lg2_sfu(r.d1sq);
                 }
             }
-            hw[i] = lw[i] = hz[i] = lz[i] = 0.0f;
+            qx2[i] = f2_pack(qx, qx);
+            qy2[i] = f2_pack(qy, qy);
+            c2[i] = f2_pack(c, c);
+            b2[i] = f2_pack(b, b);
+            hw[i] = lw[i] = hz[i] = lz[i] = zero2;
         }
 
         for (; u < seg_end; ++u) {
             const int s = (int)((u - u0) % kStages);
             const uint32_t par = (uint32_t)(((u - u0) / kStages) & 1);
             const bool ok = mbar_wait_bounded(&full[s], par, kWaitTries);
-            const Point *tile = buf + s * kDTile;
-            const int cnt = (int)min((long long)kDTile, a.n_pad - (u % a.D) * kDTile);
+            const float *X = buf + s * 3 * kDTile;
+            const float *Y = X + kDTile;
+            const float *Z = Y + kDTile;
+            const int cnt = soa_count(a, u % a.D);
             if (ok) {
-                for (int c0 = 0; c0 < cnt; c0 += kChunk) {
-                    float ps[C::kQPT], pz[C::kQPT];
+                for (int c0 = 0; c0 < cnt; c0 += kChunk2) {
+                    F2 ps[Q], pz[Q];
 #pragma unroll
-                    for (int i = 0; i < C::kQPT; ++i) ps[i] = pz[i] = 0.0f;
-#pragma unroll 8
-                    for (int jj = 0; jj < kChunk; ++jj) {
-                        const float4 p = reinterpret_cast<const float4 *>(tile)[c0 + jj];
+                    for (int i = 0; i < Q; ++i) ps[i] = pz[i] = zero2;
+#pragma unroll 4
+                    for (int jj = c0; jj < c0 + kChunk2; jj += 4) {
+                        const float4 xv = *reinterpret_cast<const float4 *>(X + jj);
+                        const float4 yv = *reinterpret_cast<const float4 *>(Y + jj);
+                        const float4 zv = *reinterpret_cast<const float4 *>(Z + jj);
+                        const F2 xs[2] = {f2_pack(xv.x, xv.y), f2_pack(xv.z, xv.w)};
+                        const F2 ys[2] = {f2_pack(yv.x, yv.y), f2_pack(yv.z, yv.w)};
+                        const F2 zs[2] = {f2_pack(zv.x, zv.y), f2_pack(zv.z, zv.w)};
 #pragma unroll
-                        for (int i = 0; i < C::kQPT; ++i) {
-                            const float d2 = dist2_f32(qx[i], qy[i], p.x, p.y);
-                            const float w = ex2_sfu(fma_rn(lg2_sfu(d2), cq[i], bq[i]));
-                            ps[i] = add_rn(ps[i], w);
-                            pz[i] = fma_rn(w, p.z, pz[i]);
+                        for (int h = 0; h < 2; ++h) {
+#pragma unroll
+                            for (int i = 0; i < Q; ++i) {
+                                const F2 dx = f2_add(qx2[i], xs[h]);
+                                const F2 dy = f2_add(qy2[i], ys[h]);
+                                const F2 d2 = f2_fma(dy, dy, f2_mul(dx, dx));
+                                float d0, d1;
+                                f2_unpack(d2, d0, d1);
+                                const F2 tt = f2_fma(f2_pack(lg2_sfu(d0), lg2_sfu(d1)), c2[i], b2[i]);
+                                float t0, t1;
+                                f2_unpack(tt, t0, t1);
+                                const F2 w = f2_pack(ex2_sfu(t0), ex2_sfu(t1));
+                                ps[i] = f2_add(ps[i], w);
+                                pz[i] = f2_fma(w, zs[h], pz[i]);
+                            }
                         }
                     }
 #pragma unroll
-                    for (int i = 0; i < C::kQPT; ++i) {
-                        comp_add(hw[i], lw[i], ps[i]);
-                        comp_add(hz[i], lz[i], pz[i]);
+                    for (int i = 0; i < Q; ++i) {
+                        f2_comp_add(hw[i], lw[i], ps[i]);
+                        f2_comp_add(hz[i], lz[i], pz[i]);
                     }
                 }
             }
@@ -188,14 +236,22 @@ __global__ void __launch_bounds__(WCfg<false>::kThreads, WCfg<false>::kMinBlocks
                 return;
             }
             if (threadIdx.x == 0 && u + kStages < u1)
-                issue_tile(a, buf + s * kDTile, &full[s], u + kStages);
+                issue_tile_soa(a, buf + s * 3 * kDTile, &full[s], u + kStages);
         }
 
         const long long slot = t + j;
 #pragma unroll
-        for (int i = 0; i < C::kQPT; ++i)
+        for (int i = 0; i < Q; ++i) {
+            float w0, w1, wl0, wl1, z0, z1, zl0, zl1;
+            f2_unpack(hw[i], w0, w1);
+            f2_unpack(lw[i], wl0, wl1);
+            f2_unpack(hz[i], z0, z1);
+            f2_unpack(lz[i], zl0, zl1);
+            comp_add(w0, wl0, w1);
+            comp_add(z0, zl0, z1);
             part[slot * C::kQTile + (long long)i * C::kThreads + threadIdx.x] =
-                make_float4(hw[i], lw[i], hz[i], lz[i]);
+                make_float4(w0, add_rn(wl0, wl1), z0, add_rn(zl0, zl1));
+        }
     }
 }
 
@@ -335,6 +391,13 @@ __global__ void k_finalize_f64(const double2 *__restrict__ part, const QRec *__r
     out_z[q] = swz / sw;
 }
 
+// Dynamic shared memory of the weighting kernels: kStages data tiles.
+template <bool F64>
+constexpr size_t stage_smem()
+{
+    return F64 ? (size_t)kStages * kDTile * sizeof(Point) : (size_t)kStages * 3 * kDTile * sizeof(float);
+}
+
 template <bool F64>
 int resident_ctas(int device)
 {
@@ -342,7 +405,7 @@ int resident_ctas(int device)
     if (device < 0 || device >= 64) return 1;
     int &c = cached[F64 ? 1 : 0][device];
     if (c) return c;
-    const size_t smem = (size_t)kStages * kDTile * sizeof(Point);
+    const size_t smem = stage_smem<F64>();
     int sms = 1, per_sm = 1;
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, device);
     if (F64) {
@@ -366,8 +429,10 @@ aidw_status run(const aidw_grid *g, const float *qx, const float *qy, long long 
     using Part = typename std::conditional<F64, double2, float4>::type;
     SKArgs a;
     a.pts = g->pts;
+    a.wt = g->wt;
+    a.n_data = g->n_data;
     a.n_pad = g->n_pad;
-    a.D = (g->n_pad + kDTile - 1) / kDTile;
+    a.D = F64 ? (g->n_pad + kDTile - 1) / kDTile : g->n_wtiles;
     a.qx = qx;
     a.qy = qy;
     a.nq = nq;
@@ -383,7 +448,7 @@ aidw_status run(const aidw_grid *g, const float *qx, const float *qy, long long 
         cudaGetLastError();
         return AIDW_ERR_OOM;
     }
-    const size_t smem = (size_t)kStages * kDTile * sizeof(Point);
+    const size_t smem = stage_smem<F64>();
     int prof = profile_begin(s);
     if (F64)
         k_weight_f64<<<(unsigned)a.G, C::kThreads, smem, s>>>(a, reinterpret_cast<double2 *>(part));
@@ -412,8 +477,10 @@ aidw_status run_scratch(const aidw_grid *g, const float *qx, const float *qy, lo
     using Part = typename std::conditional<F64, double2, float4>::type;
     SKArgs a;
     a.pts = g->pts;
+    a.wt = g->wt;
+    a.n_data = g->n_data;
     a.n_pad = g->n_pad;
-    a.D = (g->n_pad + kDTile - 1) / kDTile;
+    a.D = F64 ? (g->n_pad + kDTile - 1) / kDTile : g->n_wtiles;
     a.qx = qx;
     a.qy = qy;
     a.nq = nq;
@@ -426,7 +493,7 @@ aidw_status run_scratch(const aidw_grid *g, const float *qx, const float *qy, lo
     a.recs = recs;
     a.status = &g->dev->status;
     Part *part = static_cast<Part *>(scratch);
-    const size_t smem = (size_t)kStages * kDTile * sizeof(Point);
+    const size_t smem = stage_smem<F64>();
     int prof = profile_begin(s);
     if (F64)
         k_weight_f64<<<(unsigned)a.G, C::kThreads, smem, s>>>(a, reinterpret_cast<double2 *>(part));

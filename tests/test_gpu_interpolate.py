@@ -169,3 +169,10 @@ def test_full_size_sampled(aidw, oracle, kind):
     s2 = np.arange(0, 4096, 32)
     _check(oracle, w.x, w.y, w.z, w.qx[s64][s2], w.qy[s64][s2], 10, z64[s2], a64[s2],
            TOL_FP64, 1e-9)
+
+
+def test_pipe_rate_probe(aidw):
+    """The roofline denominator: SFU lg2/ex2 and packed-FMA lane rates."""
+    r = aidw.aidw_probe_pipe_rates()
+    assert r["lg2"] > 1 and r["ex2"] > 1 and r["ffma2_lanes"] > 1
+    assert r["ex2"] >= 0.9 * r["lg2"]
