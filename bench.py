@@ -47,7 +47,9 @@ def parse():
     ap.add_argument("--impl", choices=("ours", "reference"), default="ours")
     ap.add_argument("--n", type=int, default=1 << 20, help="data points = queries")
     ap.add_argument("--k", type=int, default=10)
-    ap.add_argument("--workload", choices=("uniform", "clustered"), default="uniform")
+    ap.add_argument("--workload", choices=("uniform", "clustered", "batch"), default="uniform")
+    ap.add_argument("--jobs", type=int, default=512, help="jobs of the batch workload")
+    ap.add_argument("--no-tune", action="store_true", help="batch: skip the autotuner")
     ap.add_argument("--e2e-steps", type=int, default=3)
     ap.add_argument("--fp64-queries", type=int, default=16384)
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
@@ -351,10 +353,81 @@ def run_ours(args):
     return 0
 
 
+def run_batch(args):
+    """Batched form: many independent jobs of uneven size per step (grid
+    builds, kNN and weighting of all jobs as one CUDA-graph replay)."""
+    import torch
+
+    import paper_1601_05904_gb300 as pkg
+    from paper_1601_05904_gb300 import binding, inputs
+
+    rank, world, local = dist_env()
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    binding.load()
+    ws = inputs.batch_jobs(n_jobs=args.jobs, seed_base=1000 + 100_000 * rank)
+    jobs = [binding.BatchJob(*(torch.from_numpy(getattr(w, a)).to(dev)
+                               for a in ("x", "y", "z", "qx", "qy")), w.k) for w in ws]
+    params = pkg.Params(k=10)
+    plan = binding.aidw_batch_plan_create(jobs, params)
+    tune_ms = None if args.no_tune else binding.aidw_batch_plan_tune(plan, jobs)
+    info = binding.aidw_batch_plan_get(plan)
+    for _ in range(args.warmup):
+        binding.aidw_batch_run(plan, jobs)
+    torch.cuda.synchronize()
+    if binding.aidw_batch_plan_status(plan) != 0:
+        raise RuntimeError("batch run reported a device error")
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+          for _ in range(args.steps)]
+    clocks = ClockSampler(local)
+    torch.cuda.synchronize()
+    clocks.start()
+    for i in range(args.steps):
+        flush.fill_(float(i))
+        ev[i][0].record()
+        binding.aidw_batch_run(plan, jobs)
+        ev[i][1].record()
+    torch.cuda.synchronize()
+    clk = clocks.stop()
+    step_ms = sum(a.elapsed_time(b) for a, b in ev) / args.steps
+    total_q = sum(w.m for w in ws)
+    rates = binding.aidw_probe_pipe_rates()
+    props = torch.cuda.get_device_properties(dev)
+    peaks = measured_peaks() or {}
+    sm_max = float(peaks.get("sm_max_mhz", 2070.0))
+    peak = 1.0 / (1.0 / rates["lg2"] + 1.0 / rates["ex2"]) * props.multi_processor_count * sm_max * 1e6
+    pairs = float(info["total_pairs"])
+    line = {"metric": "AIDW batched interpolated points/s (512 jobs, n_j log-uniform 1e3..2e5)",
+            "value": total_q / (step_ms / 1000.0), "unit": UNIT, "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": step_ms,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+            "data": "synthetic",
+            "config": {"workload": f"batch of {args.jobs} jobs, n_j = m_j log-uniform in "
+                                   "[1e3, 2e5], k_j in {8,10,16,24,32}, per-job uniform + "
+                                   "Gaussian-cluster mix in [0,1000]^2",
+                       "total_data_points": int(sum(w.n for w in ws)), "total_queries": total_q,
+                       "total_pairs": int(pairs), "cell_scale": info["cell_scale"],
+                       "knn_threads": info["knn_threads"], "tune_build_knn_ms": tune_ms,
+                       "pool_bytes": info["pool_bytes"],
+                       "l2": f"flushed between timed steps ({L2_FLUSH_BYTES >> 20} MiB write)"},
+            "pairs_per_s": pairs / (step_ms / 1000.0),
+            "roofline": {"bound": "alu", "kernel": "whole batch step (graph)",
+                         "achieved": pairs / (step_ms / 1000.0) / 1e9, "peak": peak / 1e9,
+                         "unit": "Gpair/s", "frac": pairs / (step_ms / 1000.0) / peak,
+                         "traffic": None},
+            "clocks": clk, "device": props.name}
+    plan.destroy()
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def main():
     args = parse()
     if args.impl == "reference":
         return run_reference(args)
+    if args.workload == "batch":
+        return run_batch(args)
     return run_ours(args)
 
 

@@ -153,6 +153,65 @@ aidw_status aidw_interpolate(const aidw_grid *g, const float *qx, const float *q
                              int64_t n_query, const aidw_params *p, void *out_z,
                              void *out_alpha, aidw_stream_t stream);
 
+/* ---- batched interpolation ------------------------------------------------
+ * Many independent AIDW problems ("jobs"), each with its own data points,
+ * queries and k, computed together: the method of the functions above
+ * applied to every job (the paper runs one problem at a time; batching is a
+ * throughput form of the same computation).  Every step of the path is one
+ * launch over all jobs, the all-points weighting (Eq. 1) is a single
+ * persistent launch whose work units span all jobs, and the launch sequence
+ * is captured once into a CUDA graph that each run replays.
+ *
+ * A job: x, y, z [n_data] and qx, qy [n_query] device float32 (caller-owned);
+ * out_z [n_query] device array of float32 (AIDW_FP32_COMP) or float64
+ * (AIDW_FP64_PLAIN); k <= 0 takes params->k.  n_data >= 1, 1 <= k <= 32,
+ * k <= n_data; n_query may be 0. */
+typedef struct {
+    const float *x, *y, *z;
+    int64_t n_data;
+    const float *qx, *qy;
+    int64_t n_query;
+    int k;
+    void *out_z;
+} aidw_job;
+
+/* Opaque plan: the job shapes, one pooled device allocation for every job's
+ * grid, kNN records and partial sums, the device job table and the graph. */
+typedef struct aidw_batch_plan aidw_batch_plan;
+
+/* Creates a plan for jobs with these shapes (only n_data, n_query and k are
+ * read).  Allocates the pool (cudaMalloc) and a pinned staging table. */
+aidw_status aidw_batch_plan_create(const aidw_job *jobs, int n_jobs, const aidw_params *p,
+                                   aidw_batch_plan **out);
+
+/* Runs the plan on jobs of the plan's shapes (pointers may differ from run
+ * to run): uploads the job table from pinned memory and launches the graph
+ * on `stream` (captured at the first run).  Asynchronous; the inputs must
+ * stay valid and unchanged until the stream reaches the end of the run. */
+aidw_status aidw_batch_run(aidw_batch_plan *plan, const aidw_job *jobs, aidw_stream_t stream);
+
+/* Autotuner: runs the grid build and kNN of the plan for each candidate
+ * cell-width scale (unless params->cell_scale fixed it) and kNN block size,
+ * keeps the fastest and discards the captured graph.  Synchronous.
+ * *best_ms (may be NULL) receives the best build+kNN time. */
+aidw_status aidw_batch_plan_tune(aidw_batch_plan *plan, const aidw_job *jobs,
+                                 aidw_stream_t stream, double *best_ms);
+
+/* The plan's current choices and size: cell-width scale, kNN block size,
+ * sum over jobs of n_data * n_query, pool bytes.  Any output may be NULL. */
+aidw_status aidw_batch_plan_get(const aidw_batch_plan *plan, double *cell_scale,
+                                int *knn_threads, int64_t *total_pairs, int64_t *pool_bytes);
+
+/* Synchronises the device and returns then clears the device-side errors of
+ * the last runs (any job). */
+aidw_status aidw_batch_plan_status(aidw_batch_plan *plan);
+
+aidw_status aidw_batch_plan_destroy(aidw_batch_plan *plan);
+
+/* One-shot: create a plan, run it, wait, check the device status, destroy. */
+aidw_status aidw_batch(const aidw_job *jobs, int n_jobs, const aidw_params *p,
+                       aidw_stream_t stream);
+
 /* ---- interpolation without device allocation ------------------------------
  * No counterpart in the paper; this is a library service.  Some callers
  * cannot let a library allocate device memory: an application that reserves
@@ -195,7 +254,8 @@ typedef enum {
     AIDW_STAGE_KNN = 1,        /* grid kNN + alpha                         */
     AIDW_STAGE_WEIGHT = 2,     /* all-points weighting (Eq. 1), stream-K   */
     AIDW_STAGE_FINALIZE = 3,   /* combine partial sums, divide             */
-    AIDW_STAGE_COUNT = 4
+    AIDW_STAGE_BATCH = 4,      /* one aidw_batch_run (whole graph)         */
+    AIDW_STAGE_COUNT = 5
 } aidw_stage;
 
 aidw_status aidw_profile_enable(int on);

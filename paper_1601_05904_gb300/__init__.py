@@ -16,7 +16,8 @@ def load():
 
 def __getattr__(name):
     if name.startswith("aidw_") or name in ("Params", "Grid", "AidwError", "interpolate_host",
-                                            "AIDW_FP32_COMP", "AIDW_FP64_PLAIN", "STAGES"):
+                                            "BatchJob", "BatchPlan", "AIDW_FP32_COMP",
+                                            "AIDW_FP64_PLAIN", "STAGES"):
         from . import binding
         return getattr(binding, name)
     raise AttributeError(name)

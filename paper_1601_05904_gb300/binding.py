@@ -23,7 +23,7 @@ AIDW_OK = 0
 AIDW_FP32_COMP = 0
 AIDW_FP64_PLAIN = 1
 AIDW_MAX_K = 32
-STAGES = ("grid_build", "knn", "weight", "finalize")
+STAGES = ("grid_build", "knn", "weight", "finalize", "batch")
 
 _STATUS_NAMES = {0: "AIDW_OK", 1: "AIDW_ERR_INVALID_ARG", 2: "AIDW_ERR_K_RANGE",
                  3: "AIDW_ERR_NONFINITE", 4: "AIDW_ERR_OOM", 5: "AIDW_ERR_CUDA",
@@ -77,6 +77,12 @@ class Params:
         return c
 
 
+class CJob(ctypes.Structure):
+    _fields_ = [("x", ctypes.c_void_p), ("y", ctypes.c_void_p), ("z", ctypes.c_void_p),
+                ("n_data", ctypes.c_int64), ("qx", ctypes.c_void_p), ("qy", ctypes.c_void_p),
+                ("n_query", ctypes.c_int64), ("k", ctypes.c_int), ("out_z", ctypes.c_void_p)]
+
+
 _lib = None
 _lock = threading.Lock()
 
@@ -118,6 +124,20 @@ def load(path: str | None = None):
         lib.aidw_profile_read.argtypes = [P(ctypes.c_double), P(ctypes.c_int64)]
         lib.aidw_probe_pipe_rates.restype = c_int
         lib.aidw_probe_pipe_rates.argtypes = [P(ctypes.c_double)] * 3
+        lib.aidw_batch_plan_create.restype = c_int
+        lib.aidw_batch_plan_create.argtypes = [P(CJob), c_int, P(CParams), P(vp)]
+        lib.aidw_batch_run.restype = c_int
+        lib.aidw_batch_run.argtypes = [vp, P(CJob), vp]
+        lib.aidw_batch_plan_tune.restype = c_int
+        lib.aidw_batch_plan_tune.argtypes = [vp, P(CJob), vp, P(ctypes.c_double)]
+        lib.aidw_batch_plan_get.restype = c_int
+        lib.aidw_batch_plan_get.argtypes = [vp, P(ctypes.c_double), P(c_int), P(i64), P(i64)]
+        lib.aidw_batch_plan_status.restype = c_int
+        lib.aidw_batch_plan_status.argtypes = [vp]
+        lib.aidw_batch_plan_destroy.restype = c_int
+        lib.aidw_batch_plan_destroy.argtypes = [vp]
+        lib.aidw_batch.restype = c_int
+        lib.aidw_batch.argtypes = [P(CJob), c_int, P(CParams), vp]
         _lib = lib
         return lib
 
@@ -279,6 +299,111 @@ def aidw_probe_pipe_rates() -> dict:
     r = [ctypes.c_double() for _ in range(3)]
     _check(load().aidw_probe_pipe_rates(*(ctypes.byref(v) for v in r)), "aidw_probe_pipe_rates")
     return {"lg2": r[0].value, "ex2": r[1].value, "ffma2_lanes": r[2].value}
+
+
+@dataclass
+class BatchJob:
+    """One job of a batch: device tensors (float32) and k (<= 0: params.k).
+    out_z is allocated by ``batch_jobs_alloc`` when left None."""
+    x: object
+    y: object
+    z: object
+    qx: object
+    qy: object
+    k: int = 0
+    out_z: object = None
+
+
+def _c_jobs(jobs, params: Params):
+    import torch
+    arr = (CJob * len(jobs))()
+    dt = torch.float64 if params.precision == AIDW_FP64_PLAIN else torch.float32
+    for i, j in enumerate(jobs):
+        for name in ("x", "y", "z", "qx", "qy"):
+            _f32_dev(getattr(j, name), name)
+        if j.out_z is None:
+            j.out_z = torch.empty(j.qx.numel(), dtype=dt, device=j.qx.device)
+        if j.out_z.dtype != dt or j.out_z.numel() != j.qx.numel():
+            raise TypeError(f"job {i}: out_z must be {dt} of length {j.qx.numel()}")
+        arr[i].x, arr[i].y, arr[i].z = j.x.data_ptr(), j.y.data_ptr(), j.z.data_ptr()
+        arr[i].n_data = j.x.numel()
+        arr[i].qx, arr[i].qy = j.qx.data_ptr(), j.qy.data_ptr()
+        arr[i].n_query = j.qx.numel()
+        arr[i].k = int(j.k)
+        arr[i].out_z = j.out_z.data_ptr()
+    return arr
+
+
+@dataclass
+class BatchPlan:
+    """Owner of an aidw_batch_plan handle."""
+    handle: ctypes.c_void_p
+    params: Params
+    n_jobs: int
+    _alive: bool = field(default=True, repr=False)
+
+    def destroy(self) -> None:
+        if self._alive:
+            self._alive = False
+            _check(load().aidw_batch_plan_destroy(self.handle), "aidw_batch_plan_destroy")
+
+    def __del__(self):
+        if getattr(self, "_alive", False):
+            try:
+                self._alive = False
+                load().aidw_batch_plan_destroy(self.handle)
+            except Exception:
+                pass
+
+
+def aidw_batch_plan_create(jobs, params: Params | None = None) -> BatchPlan:
+    p = params or Params()
+    arr = _c_jobs(jobs, p)
+    pc = p.to_c()
+    h = ctypes.c_void_p()
+    _check(load().aidw_batch_plan_create(arr, len(jobs), ctypes.byref(pc), ctypes.byref(h)),
+           "aidw_batch_plan_create")
+    return BatchPlan(h, p, len(jobs))
+
+
+def aidw_batch_run(plan: BatchPlan, jobs, stream=None):
+    arr = _c_jobs(jobs, plan.params)
+    _check(load().aidw_batch_run(plan.handle, arr, _stream(stream)), "aidw_batch_run")
+    return [j.out_z for j in jobs]
+
+
+def aidw_batch_plan_tune(plan: BatchPlan, jobs, stream=None) -> float:
+    arr = _c_jobs(jobs, plan.params)
+    best = ctypes.c_double()
+    _check(load().aidw_batch_plan_tune(plan.handle, arr, _stream(stream), ctypes.byref(best)),
+           "aidw_batch_plan_tune")
+    return best.value
+
+
+def aidw_batch_plan_get(plan: BatchPlan) -> dict:
+    cs, th = ctypes.c_double(), ctypes.c_int()
+    pairs, pool = ctypes.c_int64(), ctypes.c_int64()
+    _check(load().aidw_batch_plan_get(plan.handle, ctypes.byref(cs), ctypes.byref(th),
+                                      ctypes.byref(pairs), ctypes.byref(pool)),
+           "aidw_batch_plan_get")
+    return {"cell_scale": cs.value, "knn_threads": th.value, "total_pairs": pairs.value,
+            "pool_bytes": pool.value}
+
+
+def aidw_batch_plan_status(plan: BatchPlan) -> int:
+    return int(load().aidw_batch_plan_status(plan.handle))
+
+
+def aidw_batch_plan_destroy(plan: BatchPlan) -> None:
+    plan.destroy()
+
+
+def aidw_batch(jobs, params: Params | None = None, stream=None):
+    p = params or Params()
+    arr = _c_jobs(jobs, p)
+    pc = p.to_c()
+    _check(load().aidw_batch(arr, len(jobs), ctypes.byref(pc), _stream(stream)), "aidw_batch")
+    return [j.out_z for j in jobs]
 
 
 def interpolate_host(x, y, z, qx, qy, params: Params | None = None, stream=None):

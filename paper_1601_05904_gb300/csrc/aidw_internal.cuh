@@ -90,10 +90,61 @@ struct AlphaParams {
     double area_override;  // > 0 replaces the grid's area in Eq. 2
 };
 
+// One kNN job: a grid, its queries and where the results go.  Batched
+// launches index a device array of these by flat query number (q_base).
+struct KnnJob {
+    const GridDev *g;
+    const Point *pts;
+    const int *start;
+    const float *qx, *qy;
+    QRec *recs;
+    int *out_idx;
+    float *out_dist;
+    float *out_robs;
+    void *out_alpha;
+    long long nq;
+    long long q_base;
+    int k;
+    int pad_;
+};
+
+// One weighting job.  Units of all jobs are numbered job after job
+// (unit_base), and so are their query tiles (tile_base) and queries (q_base).
+struct WJob {
+    const float *wt;   // weighting tiles (float32 path)
+    const Point *pts;  // AoS points (float64 path)
+    const float *qx, *qy;
+    const QRec *recs;
+    void *out_z;
+    long long n_data, n_pad;
+    long long D, T;    // data tiles, query tiles
+    long long nq;
+    long long unit_base, tile_base, q_base;
+};
+
 // kNN (+ alpha): fills recs (if not null) and the optional public outputs.
 aidw_status knn_launch(const aidw_grid *g, const float *qx, const float *qy, long long n_query,
                        int k, bool fp64, const AlphaParams &ap, QRec *recs, int *out_idx,
                        float *out_dist, float *out_robs, void *out_alpha, cudaStream_t s);
+
+// Batched kNN over jobs[0, n_jobs) (device array) whose k all need at most
+// kmax (8, 16 or 32) slots; total_q is the sum of their query counts.
+aidw_status knn_launch_batch(const KnnJob *jobs, int n_jobs, long long total_q, int kmax,
+                             bool fp64, const AlphaParams &ap, int threads, cudaStream_t s);
+
+// Data tiles per job of the weighting stage and query tiles per job.
+long long weight_data_tiles(long long n_data, long long n_pad, bool fp64);
+long long weight_query_tile(bool fp64);
+// Persistent CTAs the weighting kernel runs with on `device`.
+int weight_resident_ctas(int device, bool fp64);
+
+// Batched weighting + finalize over jobs[0, n_jobs) (device array), total_u
+// units and total_q queries; part holds (total tiles + G) * query-tile
+// partial records.
+aidw_status weight_launch_batch(const WJob *jobs, int n_jobs, long long total_u,
+                                long long total_q, bool fp64, void *part, long long G,
+                                int *status, int device, cudaStream_t s);
+size_t weight_partial_bytes(bool fp64);  // bytes of one query tile's partials
 
 // Weighting (stream-K over all data points) + finalize.  Allocates its
 // partial-sum scratch with cudaMallocAsync on s.

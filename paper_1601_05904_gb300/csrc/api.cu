@@ -53,6 +53,11 @@ int profile_begin(cudaStream_t s)
 {
     std::lock_guard<std::mutex> lk(g_prof_mu);
     if (!g_prof_on) return -1;
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    if (cudaStreamIsCapturing(s, &cs) != cudaSuccess || cs != cudaStreamCaptureStatusNone) {
+        cudaGetLastError();
+        return -1;  // no timing events inside a graph capture
+    }
     ProfRec r;
     r.a = take_event();
     r.b = take_event();

@@ -1,0 +1,633 @@
+// Batched AIDW: many independent interpolation jobs (each its own data
+// points, queries and k) in one pass.
+//
+// A plan fixes the job shapes (n_data, n_query, k per job) and carves one
+// pooled device allocation into every job's grid arrays, kNN records and the
+// weighting partial sums.  Each step of the path is one launch over all jobs:
+// the grid-build kernels map blocks to jobs through per-job block prefixes,
+// the kNN kernels (one per top-k width class) map queries to jobs, and the
+// weighting stage is a single persistent stream-K launch over the units of
+// all jobs, so jobs of very different sizes share the GPU evenly.  The launch
+// sequence is captured once into a CUDA graph; each run uploads the job
+// table (the caller's pointers) and replays the graph.  The cell width scale
+// and the kNN block size can be chosen by a measuring autotuner.
+#include <string.h>
+
+#include <algorithm>
+#include <mutex>
+#include <new>
+#include <vector>
+
+#include "aidw_device.cuh"
+#include "aidw_internal.cuh"
+#include "grid_device.cuh"
+
+namespace aidw {
+namespace {
+
+using namespace gridk;
+
+// Everything the batched build kernels need about one job.
+struct BJob {
+    const float *x, *y, *z;
+    GridDev *g;
+    Point *pts;
+    int *start;
+    int *perm;
+    float *wt;
+    int *key, *rank, *tmp;
+    int *bsum;
+    long long n, n_pad, n_wpad, cap;
+    long long nchunks;      // scan chunks of start[0, cap]
+    long long bbox_blocks;  // blocks of the bounding-box reduction
+    long long blk_pt, blk_bbox, blk_scan, blk_pad;  // first block in each launch
+    double cell_scale, area_param;
+};
+
+// Job whose first block (field F of the table) is the largest <= b.
+template <long long BJob::*F>
+__device__ __forceinline__ int job_of_block(const BJob *__restrict__ jobs, int n_jobs, long long b)
+{
+    int lo = 0, hi = n_jobs - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (jobs[mid].*F <= b)
+            lo = mid;
+        else
+            hi = mid - 1;
+    }
+    return lo;
+}
+
+__global__ void k_b_init(const BJob *__restrict__ jobs, int n_jobs)
+{
+    const int j = blockIdx.x * blockDim.x + threadIdx.x;
+    if (j < n_jobs) grid_init(jobs[j].g, jobs[j].n);
+}
+
+__global__ void __launch_bounds__(kThreads) k_b_bbox(const BJob *__restrict__ jobs, int n_jobs)
+{
+    const BJob &J = jobs[job_of_block<&BJob::blk_bbox>(jobs, n_jobs, blockIdx.x)];
+    const long long lb = blockIdx.x - J.blk_bbox;
+    bbox_block(J.x, J.y, J.z, lb * kThreads + threadIdx.x, J.n, J.bbox_blocks * kThreads, J.g);
+}
+
+__global__ void k_b_dims(const BJob *__restrict__ jobs, int n_jobs)
+{
+    const int j = blockIdx.x * blockDim.x + threadIdx.x;
+    if (j < n_jobs) grid_dims(jobs[j].g, jobs[j].cell_scale, jobs[j].area_param, jobs[j].cap);
+}
+
+__global__ void __launch_bounds__(kThreads) k_b_keys(const BJob *__restrict__ jobs, int n_jobs)
+{
+    const BJob &J = jobs[job_of_block<&BJob::blk_pt>(jobs, n_jobs, blockIdx.x)];
+    const long long i = (blockIdx.x - J.blk_pt) * kThreads + threadIdx.x;
+    if (i >= J.n || grid_failed(J.g)) return;
+    key_one(i, J.x, J.y, J.g, J.start, J.key, J.rank);
+}
+
+__global__ void __launch_bounds__(kThreads) k_b_scan_reduce(const BJob *__restrict__ jobs,
+                                                            int n_jobs)
+{
+    const BJob &J = jobs[job_of_block<&BJob::blk_scan>(jobs, n_jobs, blockIdx.x)];
+    const long long c = blockIdx.x - J.blk_scan;
+    scan_reduce_chunk(J.start, J.cap + 1, c, J.bsum + c);
+}
+
+__global__ void __launch_bounds__(kThreads) k_b_scan_sums(const BJob *__restrict__ jobs)
+{
+    const BJob &J = jobs[blockIdx.x];
+    scan_sums(J.bsum, (int)J.nchunks);
+}
+
+__global__ void __launch_bounds__(kThreads) k_b_scan_apply(const BJob *__restrict__ jobs,
+                                                           int n_jobs)
+{
+    const BJob &J = jobs[job_of_block<&BJob::blk_scan>(jobs, n_jobs, blockIdx.x)];
+    const long long c = blockIdx.x - J.blk_scan;
+    scan_apply_chunk(J.start, J.cap + 1, c, J.bsum[c]);
+}
+
+__global__ void __launch_bounds__(kThreads) k_b_scatter(const BJob *__restrict__ jobs, int n_jobs)
+{
+    const BJob &J = jobs[job_of_block<&BJob::blk_pt>(jobs, n_jobs, blockIdx.x)];
+    const long long i = (blockIdx.x - J.blk_pt) * kThreads + threadIdx.x;
+    if (i >= J.n || grid_failed(J.g)) return;
+    scatter_one(i, J.start, J.key, J.rank, J.tmp);
+}
+
+__global__ void __launch_bounds__(kThreads) k_b_fixup(const BJob *__restrict__ jobs, int n_jobs)
+{
+    const BJob &J = jobs[job_of_block<&BJob::blk_pt>(jobs, n_jobs, blockIdx.x)];
+    const long long s = (blockIdx.x - J.blk_pt) * kThreads + threadIdx.x;
+    if (s >= J.n || grid_failed(J.g)) return;
+    fixup_one(s, J.x, J.y, J.z, J.start, J.key, J.tmp, J.pts, J.perm, J.wt);
+}
+
+__global__ void __launch_bounds__(kThreads) k_b_pad(const BJob *__restrict__ jobs, int n_jobs)
+{
+    const BJob &J = jobs[job_of_block<&BJob::blk_pad>(jobs, n_jobs, blockIdx.x)];
+    const long long i = J.n + (blockIdx.x - J.blk_pad) * kThreads + threadIdx.x;
+    pad_one(i, J.n_pad, J.n_wpad, J.pts, J.wt);
+}
+
+__global__ void k_b_status(const BJob *__restrict__ jobs, int n_jobs, int *status)
+{
+    const int j = blockIdx.x * blockDim.x + threadIdx.x;
+    if (j < n_jobs) {
+        const int s = jobs[j].g->status;
+        if (s) atomicOr(status, s);
+    }
+}
+
+constexpr double kTuneScales[] = {0.75, 1.0, 1.5, 2.0, 3.0};
+constexpr int kTuneThreads[] = {64, 128, 256};
+constexpr double kMinScale = 0.75;
+
+inline size_t align256(size_t b) { return (b + 255) / 256 * 256; }
+inline long long cdiv(long long a, long long b) { return (a + b - 1) / b; }
+
+}  // namespace
+}  // namespace aidw
+
+using namespace aidw;
+
+struct aidw_batch_plan {
+    int n_jobs = 0;
+    int device = 0;
+    bool fp64 = false;
+    bool tuned_scale = false;   // cell scale chosen by the caller
+    aidw_params params;
+    AlphaParams ap;
+    double cell_scale = 1.0;
+    int knn_threads = 128;
+    std::vector<long long> n, m;
+    std::vector<int> k;
+
+    // per-job layout (host copies of the device tables without caller pointers)
+    std::vector<BJob> bj;
+    std::vector<KnnJob> kj;   // ordered by top-k class
+    std::vector<WJob> wj;
+    std::vector<int> korder;  // job index of each kj entry
+    int kclass_begin[4] = {0, 0, 0, 0};
+    long long kclass_q[3] = {0, 0, 0};
+    long long total_pt_blocks = 0, total_bbox_blocks = 0, total_chunks = 0, total_pad_blocks = 0;
+    long long total_u = 0, total_q = 0, total_tiles = 0, G = 1;
+    long long start_ints = 0;
+
+    unsigned char *pool = nullptr;
+    size_t pool_bytes = 0;
+    int *start_pool = nullptr;
+    BJob *d_bj = nullptr;
+    KnnJob *d_kj = nullptr;
+    WJob *d_wj = nullptr;
+    GridDev *d_grids = nullptr;
+    int *d_status = nullptr;
+    void *d_part = nullptr;
+
+    unsigned char *h_stage = nullptr;  // pinned copy of the three tables
+    size_t stage_bytes = 0;
+    cudaEvent_t stage_done = nullptr;
+    bool stage_pending = false;
+
+    cudaStream_t cap_stream = nullptr;
+    cudaGraphExec_t exec = nullptr;
+};
+
+namespace {
+
+// Recomputes the cell-width dependent part of the layout (caps, chunks).
+void layout_cells(aidw_batch_plan *P)
+{
+    long long blk_scan = 0;
+    for (int j = 0; j < P->n_jobs; ++j) {
+        BJob &b = P->bj[j];
+        b.cell_scale = P->cell_scale;
+        b.cap = grid_cells_capacity(b.n, P->cell_scale);
+        b.nchunks = cdiv(b.cap + 1, kScanChunk);
+        b.blk_scan = blk_scan;
+        blk_scan += b.nchunks;
+    }
+    P->total_chunks = blk_scan;
+}
+
+// Fills the caller's pointers into the staged tables and uploads them.
+aidw_status upload_tables(aidw_batch_plan *P, const aidw_job *jobs, cudaStream_t s)
+{
+    if (P->stage_pending) {
+        const cudaError_t e = cudaEventSynchronize(P->stage_done);
+        if (e != cudaSuccess) return cuda_status(e);
+        P->stage_pending = false;
+    }
+    BJob *hb = reinterpret_cast<BJob *>(P->h_stage);
+    KnnJob *hk = reinterpret_cast<KnnJob *>(P->h_stage + sizeof(BJob) * P->n_jobs);
+    WJob *hw = reinterpret_cast<WJob *>(P->h_stage + (sizeof(BJob) + sizeof(KnnJob)) * P->n_jobs);
+    for (int j = 0; j < P->n_jobs; ++j) {
+        hb[j] = P->bj[j];
+        hb[j].x = jobs[j].x;
+        hb[j].y = jobs[j].y;
+        hb[j].z = jobs[j].z;
+        hw[j] = P->wj[j];
+        hw[j].qx = jobs[j].qx;
+        hw[j].qy = jobs[j].qy;
+        hw[j].out_z = jobs[j].out_z;
+    }
+    for (int i = 0; i < P->n_jobs; ++i) {
+        const int j = P->korder[i];
+        hk[i] = P->kj[i];
+        hk[i].qx = jobs[j].qx;
+        hk[i].qy = jobs[j].qy;
+    }
+    cudaError_t e = cudaMemcpyAsync(P->d_bj, P->h_stage, P->stage_bytes, cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess) e = cudaEventRecord(P->stage_done, s);
+    if (e != cudaSuccess) return cuda_status(e);
+    P->stage_pending = true;
+    return AIDW_OK;
+}
+
+// Enqueues the whole path on s (used for capture and for tuning).
+aidw_status enqueue(aidw_batch_plan *P, cudaStream_t s, bool knn_only)
+{
+    const int J = P->n_jobs;
+    const unsigned jb = (unsigned)cdiv(J, 128);
+    k_b_init<<<jb, 128, 0, s>>>(P->d_bj, J);
+    k_b_bbox<<<(unsigned)P->total_bbox_blocks, kThreads, 0, s>>>(P->d_bj, J);
+    k_b_dims<<<jb, 128, 0, s>>>(P->d_bj, J);
+    cudaMemsetAsync(P->start_pool, 0, sizeof(int) * (size_t)P->start_ints, s);
+    k_b_keys<<<(unsigned)P->total_pt_blocks, kThreads, 0, s>>>(P->d_bj, J);
+    k_b_scan_reduce<<<(unsigned)P->total_chunks, kThreads, 0, s>>>(P->d_bj, J);
+    k_b_scan_sums<<<(unsigned)J, kThreads, 0, s>>>(P->d_bj);
+    k_b_scan_apply<<<(unsigned)P->total_chunks, kThreads, 0, s>>>(P->d_bj, J);
+    k_b_scatter<<<(unsigned)P->total_pt_blocks, kThreads, 0, s>>>(P->d_bj, J);
+    k_b_fixup<<<(unsigned)P->total_pt_blocks, kThreads, 0, s>>>(P->d_bj, J);
+    if (P->total_pad_blocks > 0)
+        k_b_pad<<<(unsigned)P->total_pad_blocks, kThreads, 0, s>>>(P->d_bj, J);
+    aidw_status st = cuda_status(cudaGetLastError());
+    const int kmax_of_class[3] = {8, 16, 32};
+    for (int c = 0; c < 3 && st == AIDW_OK; ++c) {
+        const int b = P->kclass_begin[c], e = P->kclass_begin[c + 1];
+        if (e > b)
+            st = knn_launch_batch(P->d_kj + b, e - b, P->kclass_q[c], kmax_of_class[c], P->fp64,
+                                  P->ap, P->knn_threads, s);
+    }
+    if (st != AIDW_OK || knn_only) return st;
+    st = weight_launch_batch(P->d_wj, J, P->total_u, P->total_q, P->fp64, P->d_part, P->G,
+                             P->d_status, P->device, s);
+    if (st != AIDW_OK) return st;
+    k_b_status<<<jb, 128, 0, s>>>(P->d_bj, J, P->d_status);
+    return cuda_status(cudaGetLastError());
+}
+
+aidw_status capture(aidw_batch_plan *P)
+{
+    if (P->exec) {
+        cudaGraphExecDestroy(P->exec);
+        P->exec = nullptr;
+    }
+    cudaGraph_t graph = nullptr;
+    cudaError_t e = cudaStreamBeginCapture(P->cap_stream, cudaStreamCaptureModeThreadLocal);
+    if (e != cudaSuccess) return cuda_status(e);
+    const aidw_status st = enqueue(P, P->cap_stream, false);
+    e = cudaStreamEndCapture(P->cap_stream, &graph);
+    if (st != AIDW_OK) {
+        if (graph) cudaGraphDestroy(graph);
+        return st;
+    }
+    if (e != cudaSuccess) return cuda_status(e);
+    e = cudaGraphInstantiate(&P->exec, graph, 0);
+    cudaGraphDestroy(graph);
+    return cuda_status(e);
+}
+
+aidw_status check_jobs(const aidw_batch_plan *P, const aidw_job *jobs, int n_jobs)
+{
+    if (!jobs || n_jobs != P->n_jobs) return AIDW_ERR_INVALID_ARG;
+    for (int j = 0; j < n_jobs; ++j) {
+        const aidw_job &J = jobs[j];
+        const int k = J.k > 0 ? J.k : P->params.k;
+        if (J.n_data != P->n[j] || J.n_query != P->m[j] || k != P->k[j]) return AIDW_ERR_INVALID_ARG;
+        if (!J.x || !J.y || !J.z) return AIDW_ERR_INVALID_ARG;
+        if (J.n_query > 0 && (!J.qx || !J.qy || !J.out_z)) return AIDW_ERR_INVALID_ARG;
+    }
+    return AIDW_OK;
+}
+
+void free_plan(aidw_batch_plan *P)
+{
+    if (!P) return;
+    if (P->exec) cudaGraphExecDestroy(P->exec);
+    if (P->cap_stream) cudaStreamDestroy(P->cap_stream);
+    if (P->stage_done) cudaEventDestroy(P->stage_done);
+    if (P->h_stage) cudaFreeHost(P->h_stage);
+    if (P->pool) cudaFree(P->pool);
+    delete P;
+}
+
+}  // namespace
+
+extern "C" {
+
+aidw_status aidw_batch_plan_create(const aidw_job *jobs, int n_jobs, const aidw_params *p,
+                                   aidw_batch_plan **out)
+{
+    if (!out) return AIDW_ERR_INVALID_ARG;
+    *out = nullptr;
+    if (!jobs || n_jobs < 1 || n_jobs > (1 << 20)) return AIDW_ERR_INVALID_ARG;
+    aidw_status st = api_detail::check_params(p, false);
+    if (st != AIDW_OK) return st;
+    for (int j = 0; j < n_jobs; ++j) {
+        const long long n = jobs[j].n_data, m = jobs[j].n_query;
+        const int k = jobs[j].k > 0 ? jobs[j].k : p->k;
+        if (n < 1 || n > 0x7fffffffLL - 1024 || m < 0 || m > 0x7fffffffLL) return AIDW_ERR_INVALID_ARG;
+        if (k < 1 || k > AIDW_MAX_K || k > n) return AIDW_ERR_K_RANGE;
+    }
+    aidw_batch_plan *P = new (std::nothrow) aidw_batch_plan();
+    if (!P) return AIDW_ERR_OOM;
+    P->n_jobs = n_jobs;
+    P->params = *p;
+    P->ap = api_detail::alpha_params(p);
+    P->fp64 = p->precision == AIDW_FP64_PLAIN;
+    P->tuned_scale = p->cell_scale > 0.0;
+    P->cell_scale = p->cell_scale > 0.0 ? p->cell_scale : 1.0;
+    cudaGetDevice(&P->device);
+    P->n.resize(n_jobs);
+    P->m.resize(n_jobs);
+    P->k.resize(n_jobs);
+    P->bj.assign(n_jobs, BJob());
+    P->wj.assign(n_jobs, WJob());
+    for (int j = 0; j < n_jobs; ++j) {
+        P->n[j] = jobs[j].n_data;
+        P->m[j] = jobs[j].n_query;
+        P->k[j] = jobs[j].k > 0 ? jobs[j].k : p->k;
+    }
+
+    // ---- sizes and block prefixes ----
+    const long long qt = weight_query_tile(P->fp64);
+    long long blk_pt = 0, blk_bbox = 0, blk_pad = 0, ubase = 0, tbase = 0, qbase = 0;
+    size_t off = 0;
+    auto take = [&](size_t bytes) {
+        const size_t o = off;
+        off += align256(bytes);
+        return o;
+    };
+    // the start region is sized for the smallest scale the tuner may pick
+    const double scale_for_cap = P->tuned_scale ? P->cell_scale : std::min(kMinScale, P->cell_scale);
+    std::vector<size_t> o_pts(n_jobs), o_wt(n_jobs), o_start(n_jobs), o_perm(n_jobs),
+        o_key(n_jobs), o_rank(n_jobs), o_tmp(n_jobs), o_bsum(n_jobs), o_rec(n_jobs);
+    const size_t o_grids = take(sizeof(GridDev) * (size_t)n_jobs);
+    long long start_ints = 0;
+    for (int j = 0; j < n_jobs; ++j) {
+        BJob &b = P->bj[j];
+        memset(&b, 0, sizeof(b));
+        b.n = P->n[j];
+        b.n_pad = cdiv(b.n, 32) * 32;
+        const long long nwt = cdiv(b.n, kWeightTile);
+        b.n_wpad = nwt * kWeightTile;
+        b.area_param = p->area > 0.0 ? p->area : 0.0;
+        b.bbox_blocks = std::min<long long>(cdiv(b.n, kThreads), 64);
+        b.blk_pt = blk_pt;
+        blk_pt += cdiv(b.n, kThreads);
+        b.blk_bbox = blk_bbox;
+        blk_bbox += b.bbox_blocks;
+        const long long pads = std::max(b.n_pad, b.n_wpad) - b.n;
+        b.blk_pad = blk_pad;
+        blk_pad += cdiv(pads, kThreads);
+        const long long cap_max = grid_cells_capacity(b.n, scale_for_cap);
+        o_pts[j] = take(sizeof(Point) * (size_t)b.n_pad);
+        o_wt[j] = take(sizeof(float) * 3 * (size_t)b.n_wpad);
+        o_perm[j] = take(sizeof(int) * (size_t)b.n);
+        o_key[j] = take(sizeof(int) * (size_t)b.n);
+        o_rank[j] = take(sizeof(int) * (size_t)b.n);
+        o_tmp[j] = take(sizeof(int) * (size_t)b.n);
+        o_bsum[j] = take(sizeof(int) * (size_t)cdiv(cap_max + 1, kScanChunk));
+        o_rec[j] = take(sizeof(QRec) * (size_t)std::max<long long>(P->m[j], 1));
+        o_start[j] = (size_t)start_ints;  // in ints, inside the start region
+        start_ints += (cap_max + 1 + 63) / 64 * 64;
+
+        WJob &w = P->wj[j];
+        memset(&w, 0, sizeof(w));
+        w.n_data = b.n;
+        w.n_pad = b.n_pad;
+        w.D = weight_data_tiles(b.n, b.n_pad, P->fp64);
+        w.nq = P->m[j];
+        w.T = cdiv(w.nq, qt);
+        w.unit_base = ubase;
+        w.tile_base = tbase;
+        w.q_base = qbase;
+        ubase += w.T * w.D;
+        tbase += w.T;
+        qbase += w.nq;
+    }
+    P->total_pt_blocks = blk_pt;
+    P->total_bbox_blocks = blk_bbox;
+    P->total_pad_blocks = blk_pad;
+    P->total_u = ubase;
+    P->total_tiles = tbase;
+    P->total_q = qbase;
+    P->start_ints = start_ints;
+    P->G = std::max<long long>(1, std::min<long long>(weight_resident_ctas(P->device, P->fp64),
+                                                      std::max<long long>(ubase, 1)));
+    const size_t o_startreg = take(sizeof(int) * (size_t)start_ints);
+    const size_t o_part = take(weight_partial_bytes(P->fp64) * (size_t)(P->total_tiles + P->G));
+    const size_t o_tables = take((sizeof(BJob) + sizeof(KnnJob) + sizeof(WJob)) * (size_t)n_jobs);
+    const size_t o_status = take(sizeof(int));
+    P->pool_bytes = off;
+
+    cudaError_t e = cudaMalloc((void **)&P->pool, P->pool_bytes);
+    if (e == cudaSuccess) e = cudaMallocHost((void **)&P->h_stage,
+                                             (sizeof(BJob) + sizeof(KnnJob) + sizeof(WJob)) * (size_t)n_jobs);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&P->stage_done, cudaEventDisableTiming);
+    if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&P->cap_stream, cudaStreamNonBlocking);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        free_plan(P);
+        return e == cudaErrorMemoryAllocation ? AIDW_ERR_OOM : AIDW_ERR_CUDA;
+    }
+    unsigned char *base = P->pool;
+    P->d_grids = reinterpret_cast<GridDev *>(base + o_grids);
+    P->start_pool = reinterpret_cast<int *>(base + o_startreg);
+    P->d_part = base + o_part;
+    P->d_bj = reinterpret_cast<BJob *>(base + o_tables);
+    P->d_kj = reinterpret_cast<KnnJob *>(base + o_tables + sizeof(BJob) * n_jobs);
+    P->d_wj = reinterpret_cast<WJob *>(base + o_tables + (sizeof(BJob) + sizeof(KnnJob)) * n_jobs);
+    P->d_status = reinterpret_cast<int *>(base + o_status);
+    P->stage_bytes = (sizeof(BJob) + sizeof(KnnJob) + sizeof(WJob)) * (size_t)n_jobs;
+    for (int j = 0; j < n_jobs; ++j) {
+        BJob &b = P->bj[j];
+        b.g = P->d_grids + j;
+        b.pts = reinterpret_cast<Point *>(base + o_pts[j]);
+        b.wt = reinterpret_cast<float *>(base + o_wt[j]);
+        b.perm = reinterpret_cast<int *>(base + o_perm[j]);
+        b.key = reinterpret_cast<int *>(base + o_key[j]);
+        b.rank = reinterpret_cast<int *>(base + o_rank[j]);
+        b.tmp = reinterpret_cast<int *>(base + o_tmp[j]);
+        b.bsum = reinterpret_cast<int *>(base + o_bsum[j]);
+        b.start = P->start_pool + o_start[j];
+        WJob &w = P->wj[j];
+        w.wt = b.wt;
+        w.pts = b.pts;
+        w.recs = reinterpret_cast<QRec *>(base + o_rec[j]);
+    }
+    layout_cells(P);
+
+    // kNN table ordered by top-k class (8, 16, 32 slots)
+    P->korder.clear();
+    P->kj.clear();
+    for (int c = 0; c < 3; ++c) {
+        P->kclass_begin[c] = (int)P->korder.size();
+        long long qb = 0;
+        for (int j = 0; j < n_jobs; ++j) {
+            const int k = P->k[j];
+            const int cls = k <= 8 ? 0 : (k <= 16 ? 1 : 2);
+            if (cls != c || P->m[j] == 0) continue;
+            KnnJob kj;
+            memset(&kj, 0, sizeof(kj));
+            kj.g = P->bj[j].g;
+            kj.pts = P->bj[j].pts;
+            kj.start = P->bj[j].start;
+            kj.recs = const_cast<QRec *>(P->wj[j].recs);
+            kj.nq = P->m[j];
+            kj.q_base = qb;
+            kj.k = k;
+            qb += P->m[j];
+            P->kj.push_back(kj);
+            P->korder.push_back(j);
+        }
+        P->kclass_q[c] = qb;
+    }
+    P->kclass_begin[3] = (int)P->korder.size();
+    // jobs without queries still need a kNN table slot for the upload layout
+    while ((int)P->kj.size() < n_jobs) {
+        KnnJob kj;
+        memset(&kj, 0, sizeof(kj));
+        P->kj.push_back(kj);
+        P->korder.push_back(0);
+    }
+    // warm the weighting kernel's attributes before any capture
+    weight_resident_ctas(P->device, P->fp64);
+    *out = P;
+    return AIDW_OK;
+}
+
+aidw_status aidw_batch_run(aidw_batch_plan *plan, const aidw_job *jobs, aidw_stream_t stream)
+{
+    if (!plan) return AIDW_ERR_INVALID_ARG;
+    aidw_status st = check_jobs(plan, jobs, jobs ? plan->n_jobs : 0);
+    if (st != AIDW_OK) return st;
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    if (!plan->exec) {
+        st = capture(plan);
+        if (st != AIDW_OK) return st;
+    }
+    st = upload_tables(plan, jobs, s);
+    if (st != AIDW_OK) return st;
+    const int prof = profile_begin(s);
+    st = cuda_status(cudaGraphLaunch(plan->exec, s));
+    profile_end(prof, s, AIDW_STAGE_BATCH, 1);
+    return st;
+}
+
+aidw_status aidw_batch_plan_tune(aidw_batch_plan *plan, const aidw_job *jobs,
+                                 aidw_stream_t stream, double *best_ms)
+{
+    if (!plan) return AIDW_ERR_INVALID_ARG;
+    aidw_status st = check_jobs(plan, jobs, jobs ? plan->n_jobs : 0);
+    if (st != AIDW_OK) return st;
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    cudaEvent_t a = nullptr, b = nullptr;
+    cudaEventCreate(&a);
+    cudaEventCreate(&b);
+    const double old_scale = plan->cell_scale;
+    const int old_threads = plan->knn_threads;
+    double best = 1e30, best_scale = old_scale;
+    int best_threads = old_threads;
+    for (double sc : kTuneScales) {
+        if (plan->tuned_scale && sc != plan->params.cell_scale) continue;
+        plan->cell_scale = plan->tuned_scale ? plan->params.cell_scale : sc;
+        layout_cells(plan);
+        for (int th : kTuneThreads) {
+            plan->knn_threads = th;
+            st = upload_tables(plan, jobs, s);
+            if (st != AIDW_OK) break;
+            float ms = 0.0f;
+            for (int rep = 0; rep < 2 && st == AIDW_OK; ++rep) {
+                cudaEventRecord(a, s);
+                st = enqueue(plan, s, true);
+                cudaEventRecord(b, s);
+                if (cudaEventSynchronize(b) != cudaSuccess) st = AIDW_ERR_CUDA;
+                cudaEventElapsedTime(&ms, a, b);
+            }
+            if (st != AIDW_OK) break;
+            if (ms < best) {
+                best = ms;
+                best_scale = plan->cell_scale;
+                best_threads = th;
+            }
+        }
+        if (st != AIDW_OK) break;
+    }
+    cudaEventDestroy(a);
+    cudaEventDestroy(b);
+    plan->cell_scale = st == AIDW_OK ? best_scale : old_scale;
+    plan->knn_threads = st == AIDW_OK ? best_threads : old_threads;
+    layout_cells(plan);
+    if (plan->exec) {
+        cudaGraphExecDestroy(plan->exec);
+        plan->exec = nullptr;
+    }
+    if (best_ms) *best_ms = best;
+    return st;
+}
+
+aidw_status aidw_batch_plan_get(const aidw_batch_plan *plan, double *cell_scale,
+                                int *knn_threads, int64_t *total_pairs, int64_t *pool_bytes)
+{
+    if (!plan) return AIDW_ERR_INVALID_ARG;
+    if (cell_scale) *cell_scale = plan->cell_scale;
+    if (knn_threads) *knn_threads = plan->knn_threads;
+    if (total_pairs) {
+        long long t = 0;
+        for (int j = 0; j < plan->n_jobs; ++j) t += plan->n[j] * plan->m[j];
+        *total_pairs = t;
+    }
+    if (pool_bytes) *pool_bytes = (int64_t)plan->pool_bytes;
+    return AIDW_OK;
+}
+
+aidw_status aidw_batch_plan_status(aidw_batch_plan *plan)
+{
+    if (!plan) return AIDW_ERR_INVALID_ARG;
+    cudaError_t e = cudaDeviceSynchronize();
+    int status = 0;
+    if (e == cudaSuccess) e = cudaMemcpy(&status, plan->d_status, sizeof(int), cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) return cuda_status(e);
+    const int zero = 0;
+    cudaMemcpy(plan->d_status, &zero, sizeof(int), cudaMemcpyHostToDevice);
+    if (status & kStatusTimeout) return AIDW_ERR_TIMEOUT;
+    if (status & (kStatusNonfiniteData | kStatusNonfiniteQuery)) return AIDW_ERR_NONFINITE;
+    if (status & kStatusCapacity) return AIDW_ERR_INVALID_ARG;
+    return AIDW_OK;
+}
+
+aidw_status aidw_batch_plan_destroy(aidw_batch_plan *plan)
+{
+    if (!plan) return AIDW_ERR_INVALID_ARG;
+    cudaDeviceSynchronize();
+    free_plan(plan);
+    return AIDW_OK;
+}
+
+aidw_status aidw_batch(const aidw_job *jobs, int n_jobs, const aidw_params *p,
+                       aidw_stream_t stream)
+{
+    aidw_batch_plan *plan = nullptr;
+    aidw_status st = aidw_batch_plan_create(jobs, n_jobs, p, &plan);
+    if (st != AIDW_OK) return st;
+    st = aidw_batch_run(plan, jobs, stream);
+    if (st == AIDW_OK) st = cuda_status(cudaStreamSynchronize(reinterpret_cast<cudaStream_t>(stream)));
+    if (st == AIDW_OK) st = aidw_batch_plan_status(plan);
+    aidw_batch_plan_destroy(plan);
+    return st;
+}
+
+}  // extern "C"

@@ -1,0 +1,303 @@
+// Per-element and per-block bodies of the even-grid build (Sec. 3.2.1-3.2.3,
+// 4.1.1-4.1.3 of arXiv 1601.05904), shared by the single-grid kernels
+// (grid_build.cu) and the batched kernels that build many grids in one
+// launch per step (batch.cu).
+#pragma once
+
+#include <float.h>
+#include <math.h>
+
+#include "aidw_internal.cuh"
+
+namespace aidw {
+namespace gridk {
+
+constexpr int kThreads = 256;
+constexpr int kScanItems = 16;                     // per thread
+constexpr int kScanChunk = kThreads * kScanItems;  // per block
+
+// Order-preserving integer encoding of float32 for atomicMin/atomicMax.
+__device__ __forceinline__ int enc_float(float f)
+{
+    const int b = __float_as_int(f);
+    return b >= 0 ? b : (b ^ 0x7FFFFFFF);
+}
+__device__ __forceinline__ float dec_float(int e)
+{
+    return __int_as_float(e >= 0 ? e : (e ^ 0x7FFFFFFF));
+}
+
+__device__ __forceinline__ void grid_init(GridDev *g, long long n)
+{
+    g->enc_min_x = 0x7FFFFFFF;
+    g->enc_min_y = 0x7FFFFFFF;
+    g->enc_max_x = (int)0x80000000;
+    g->enc_max_y = (int)0x80000000;
+    g->n_data = n;
+    g->status = 0;
+}
+
+// Bounding box of points [first, n) visited with the given stride by this
+// block, merged into g with atomics; also flags non-finite x, y or z.
+// Called by every thread of a block of kThreads threads.
+__device__ __forceinline__ void bbox_block(const float *__restrict__ x, const float *__restrict__ y,
+                                           const float *__restrict__ z, long long first,
+                                           long long n, long long stride, GridDev *g)
+{
+    float mnx = FLT_MAX, mny = FLT_MAX, mxx = -FLT_MAX, mxy = -FLT_MAX;
+    int bad = 0;
+    for (long long i = first; i < n; i += stride) {
+        const float xi = __ldg(x + i), yi = __ldg(y + i), zi = __ldg(z + i);
+        if (!isfinite(xi) || !isfinite(yi) || !isfinite(zi)) {
+            bad = 1;
+            continue;
+        }
+        mnx = fminf(mnx, xi);
+        mxx = fmaxf(mxx, xi);
+        mny = fminf(mny, yi);
+        mxy = fmaxf(mxy, yi);
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+        mnx = fminf(mnx, __shfl_xor_sync(0xffffffffu, mnx, o));
+        mxx = fmaxf(mxx, __shfl_xor_sync(0xffffffffu, mxx, o));
+        mny = fminf(mny, __shfl_xor_sync(0xffffffffu, mny, o));
+        mxy = fmaxf(mxy, __shfl_xor_sync(0xffffffffu, mxy, o));
+    }
+    bad = __any_sync(0xffffffffu, bad);
+    __shared__ float s[4][kThreads / 32];
+    __shared__ int sbad;
+    if (threadIdx.x == 0) sbad = 0;
+    __syncthreads();
+    const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+    if (l == 0) {
+        s[0][w] = mnx;
+        s[1][w] = mxx;
+        s[2][w] = mny;
+        s[3][w] = mxy;
+        if (bad) sbad = 1;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        for (int i = 1; i < kThreads / 32; ++i) {
+            mnx = fminf(mnx, s[0][i]);
+            mxx = fmaxf(mxx, s[1][i]);
+            mny = fminf(mny, s[2][i]);
+            mxy = fmaxf(mxy, s[3][i]);
+        }
+        atomicMin(&g->enc_min_x, enc_float(mnx));
+        atomicMax(&g->enc_max_x, enc_float(mxx));
+        atomicMin(&g->enc_min_y, enc_float(mny));
+        atomicMax(&g->enc_max_y, enc_float(mxy));
+        if (sbad) atomicOr(&g->status, kStatusNonfiniteData);
+    }
+}
+
+// Grid dimensions.  cap is the capacity of the cell arrays: if the box's
+// aspect ratio or an explicit area would need more cells, the width is
+// doubled until it fits (the kNN result does not depend on it).
+__device__ __forceinline__ void grid_dims(GridDev *g, double cell_scale, double area_param,
+                                          long long cap)
+{
+    if (g->status & kStatusNonfiniteData) return;
+    const double minx = (double)dec_float(g->enc_min_x), maxx = (double)dec_float(g->enc_max_x);
+    const double miny = (double)dec_float(g->enc_min_y), maxy = (double)dec_float(g->enc_max_y);
+    const double W = maxx - minx, H = maxy - miny;
+    const double n = (double)g->n_data;
+    const double area = area_param > 0.0 ? area_param : W * H;
+    const double r_exp = (area > 0.0) ? 1.0 / (2.0 * sqrt(n / area)) : 0.0;  // Eq. 2
+    double cw = cell_scale * r_exp;
+    if (!(cw > 0.0)) {
+        const double side = W > H ? W : H;
+        cw = side > 0.0 ? cell_scale * side / (2.0 * n) : 1.0;
+    }
+    for (int it = 0; it < 2100; ++it) {
+        const double nc = floor((W + cw) / cw), nr = floor((H + cw) / cw);
+        if (nc * nr <= (double)cap) break;
+        cw = cw * 2.0;
+    }
+    g->min_x = minx;
+    g->min_y = miny;
+    g->max_x = maxx;
+    g->max_y = maxy;
+    g->area = area;
+    g->r_exp = r_exp;
+    g->cw = cw;
+    g->n_col = (long long)((W + cw) / cw);
+    g->n_row = (long long)((H + cw) / cw);
+    g->n_cells = g->n_col * g->n_row;
+    if (g->n_cells > cap) atomicOr(&g->status, kStatusCapacity);
+}
+
+__device__ __forceinline__ bool grid_failed(const GridDev *g)
+{
+    return (g->status & (kStatusNonfiniteData | kStatusCapacity)) != 0;
+}
+
+// Cell of point i and its (unstable) rank among the points of that cell.
+__device__ __forceinline__ void key_one(long long i, const float *__restrict__ x,
+                                        const float *__restrict__ y, const GridDev *g,
+                                        int *__restrict__ count, int *__restrict__ key,
+                                        int *__restrict__ rank)
+{
+    const double minx = g->min_x, miny = g->min_y, cw = g->cw;
+    const long long nc = g->n_col, nr = g->n_row;
+    long long col = (long long)floor(((double)x[i] - minx) / cw);
+    long long row = (long long)floor(((double)y[i] - miny) / cw);
+    col = col < 0 ? 0 : (col > nc - 1 ? nc - 1 : col);
+    row = row < 0 ? 0 : (row > nr - 1 ? nr - 1 : row);
+    const int c = (int)(row * nc + col);
+    key[i] = c;
+    rank[i] = atomicAdd(count + c, 1);
+}
+
+// Block-wide exclusive scan of one value per thread; total gets the sum.
+__device__ __forceinline__ int block_exclusive_scan(int v, int &total)
+{
+    __shared__ int warp_tot[kThreads / 32];
+    const int l = threadIdx.x & 31, w = threadIdx.x >> 5;
+    int incl = v;
+    for (int o = 1; o < 32; o <<= 1) {
+        const int t = __shfl_up_sync(0xffffffffu, incl, o);
+        if (l >= o) incl += t;
+    }
+    if (l == 31) warp_tot[w] = incl;
+    __syncthreads();
+    if (w == 0) {
+        const int t = l < kThreads / 32 ? warp_tot[l] : 0;
+        int ti = t;
+        for (int o = 1; o < 32; o <<= 1) {
+            const int u = __shfl_up_sync(0xffffffffu, ti, o);
+            if (l >= o) ti += u;
+        }
+        if (l < kThreads / 32) warp_tot[l] = ti - t;  // exclusive warp offsets
+        if (l == kThreads / 32 - 1) total = ti;
+    }
+    __syncthreads();
+    const int r = warp_tot[w] + incl - v;
+    __syncthreads();
+    return r;
+}
+
+// Sum of chunk `chunk` (kScanChunk elements) of a[0, len) -> *out (block-wide).
+__device__ __forceinline__ void scan_reduce_chunk(const int *__restrict__ a, long long len,
+                                                  long long chunk, int *out)
+{
+    const long long base = chunk * kScanChunk;
+    int s = 0;
+#pragma unroll
+    for (int j = 0; j < kScanItems; ++j) {
+        const long long i = base + (long long)j * kThreads + threadIdx.x;
+        if (i < len) s += a[i];
+    }
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+    __shared__ int ws[kThreads / 32];
+    if ((threadIdx.x & 31) == 0) ws[threadIdx.x >> 5] = s;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        int t = 0;
+        for (int i = 0; i < kThreads / 32; ++i) t += ws[i];
+        *out = t;
+    }
+}
+
+// Exclusive scan of the nb chunk sums in place (block-wide).
+__device__ __forceinline__ void scan_sums(int *block_sum, int nb)
+{
+    __shared__ int carry;
+    __shared__ int tot;
+    if (threadIdx.x == 0) carry = 0;
+    __syncthreads();
+    for (int base = 0; base < nb; base += kThreads) {
+        const int i = base + threadIdx.x;
+        const int v = i < nb ? block_sum[i] : 0;
+        const int ex = block_exclusive_scan(v, tot);
+        if (i < nb) block_sum[i] = carry + ex;
+        __syncthreads();
+        if (threadIdx.x == 0) carry += tot;
+        __syncthreads();
+    }
+}
+
+// Exclusive scan of chunk `chunk` of a[0, len) in place, starting at offset
+// (block-wide; each thread owns kScanItems consecutive elements).
+__device__ __forceinline__ void scan_apply_chunk(int *__restrict__ a, long long len,
+                                                 long long chunk, int offset)
+{
+    __shared__ int tot;
+    const long long base = chunk * kScanChunk + (long long)threadIdx.x * kScanItems;
+    int v[kScanItems];
+    int s = 0;
+#pragma unroll
+    for (int j = 0; j < kScanItems; ++j) {
+        v[j] = (base + j < len) ? a[base + j] : 0;
+        s += v[j];
+    }
+    int run = offset + block_exclusive_scan(s, tot);
+#pragma unroll
+    for (int j = 0; j < kScanItems; ++j) {
+        if (base + j < len) a[base + j] = run;
+        run += v[j];
+    }
+}
+
+__device__ __forceinline__ void scatter_one(long long i, const int *__restrict__ start,
+                                            const int *__restrict__ key,
+                                            const int *__restrict__ rank, int *__restrict__ tmp)
+{
+    tmp[start[key[i]] + rank[i]] = (int)i;
+}
+
+// Position s holds some point i of cell c = key[i]; its stable place is the
+// head of c plus the number of indices smaller than i in c's segment.  The
+// point is written there in both layouts.
+__device__ __forceinline__ void fixup_one(long long s, const float *__restrict__ x,
+                                          const float *__restrict__ y,
+                                          const float *__restrict__ z,
+                                          const int *__restrict__ start,
+                                          const int *__restrict__ key,
+                                          const int *__restrict__ tmp, Point *__restrict__ pts,
+                                          int *__restrict__ perm, float *__restrict__ wt)
+{
+    const int i = tmp[s];
+    const int c = key[i];
+    const int a = start[c], b = start[c + 1];
+    int r = 0;
+    for (int t = a; t < b; ++t) r += (tmp[t] < i);
+    Point p;
+    p.x = x[i];
+    p.y = y[i];
+    p.z = z[i];
+    p.idx = i;
+    const long long pos = (long long)a + r;
+    pts[pos] = p;
+    perm[pos] = i;
+    float *tile = wt + (pos / kWeightTile) * (3 * kWeightTile) + pos % kWeightTile;
+    tile[0] = -p.x;
+    tile[kWeightTile] = -p.y;
+    tile[2 * kWeightTile] = p.z;
+}
+
+// Padding position i >= n: +inf coordinates, whose weight is exactly 0
+// (d^2 = inf, log2 = inf, exp2(-inf) = 0), in both layouts.
+__device__ __forceinline__ void pad_one(long long i, long long n_pad, long long n_wpad,
+                                        Point *__restrict__ pts, float *__restrict__ wt)
+{
+    const float inf = __int_as_float(0x7f800000);
+    if (i < n_pad) {
+        Point p;
+        p.x = inf;
+        p.y = inf;
+        p.z = 0.0f;
+        p.idx = -1;
+        pts[i] = p;
+    }
+    if (i < n_wpad) {
+        float *tile = wt + (i / kWeightTile) * (3 * kWeightTile) + i % kWeightTile;
+        tile[0] = -inf;
+        tile[kWeightTile] = -inf;
+        tile[2 * kWeightTile] = 0.0f;
+    }
+}
+
+}  // namespace gridk
+}  // namespace aidw

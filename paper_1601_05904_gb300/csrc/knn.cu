@@ -24,6 +24,7 @@
 // stage: alpha, the smallest squared distance and the mean z of data points
 // at distance 0 (the limit of Eq. 1 when the query coincides with data).
 #include <math.h>
+#include <string.h>
 
 #include <algorithm>
 
@@ -34,7 +35,8 @@ namespace aidw {
 
 namespace {
 
-constexpr int kKnnThreads = 128;
+constexpr int kKnnThreads = 128;      // single-job launches
+constexpr int kKnnMaxThreads = 256;   // largest block of batched launches
 
 template <bool F64>
 struct DistT;
@@ -57,18 +59,42 @@ struct DistT<true> {
     static __device__ __forceinline__ double inf() { return __longlong_as_double(0x7ff0000000000000LL); }
 };
 
+// Job whose flat query range [q_base, q_base + nq) contains gq.
+__device__ __forceinline__ int knn_job_of(const KnnJob *__restrict__ jobs, int n_jobs,
+                                          long long gq)
+{
+    int lo = 0, hi = n_jobs - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (jobs[mid].q_base <= gq)
+            lo = mid;
+        else
+            hi = mid - 1;
+    }
+    return lo;
+}
+
 template <bool F64, int KMAX>
-__global__ void __launch_bounds__(kKnnThreads)
-    k_knn(const GridDev *__restrict__ g, const Point *__restrict__ pts,
-          const int *__restrict__ start, const float *__restrict__ qxa,
-          const float *__restrict__ qya, long long nq, int k, AlphaParams ap,
-          QRec *__restrict__ recs, int *__restrict__ out_idx, float *__restrict__ out_dist,
-          float *__restrict__ out_robs, void *__restrict__ out_alpha)
+__global__ void __launch_bounds__(kKnnMaxThreads)
+    k_knn(KnnJob job0, const KnnJob *__restrict__ jobs, int n_jobs, long long total_q,
+          AlphaParams ap)
 {
     using D = typename DistT<F64>::T;
-    const long long q = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    if (q >= nq) return;
-    const float qx = qxa[q], qy = qya[q];
+    const long long gq = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (gq >= total_q) return;
+    // single-job launches pass the job by value and no table
+    const KnnJob J = jobs ? jobs[knn_job_of(jobs, n_jobs, gq)] : job0;
+    const long long q = gq - J.q_base;
+    const GridDev *__restrict__ g = J.g;
+    const Point *__restrict__ pts = J.pts;
+    const int *__restrict__ start = J.start;
+    const int k = J.k;
+    QRec *__restrict__ recs = J.recs;
+    int *__restrict__ out_idx = J.out_idx;
+    float *__restrict__ out_dist = J.out_dist;
+    float *__restrict__ out_robs = J.out_robs;
+    void *__restrict__ out_alpha = J.out_alpha;
+    const float qx = J.qx[q], qy = J.qy[q];
     const double nanv = __longlong_as_double(0x7ff8000000000000LL);
 
     if (!isfinite(qx) || !isfinite(qy)) {
@@ -238,27 +264,23 @@ __global__ void __launch_bounds__(kKnnThreads)
 }
 
 template <bool F64, int KMAX>
-void launch_knn(const aidw_grid *g, const float *qx, const float *qy, long long nq, int k,
-                const AlphaParams &ap, QRec *recs, int *out_idx, float *out_dist,
-                float *out_robs, void *out_alpha, cudaStream_t s)
+void launch_knn(const KnnJob &job0, const KnnJob *jobs, int n_jobs, long long total_q,
+                const AlphaParams &ap, int threads, cudaStream_t s)
 {
-    const unsigned blocks = (unsigned)((nq + kKnnThreads - 1) / kKnnThreads);
-    k_knn<F64, KMAX><<<blocks, kKnnThreads, 0, s>>>(g->dev, g->pts, g->cell_start, qx, qy, nq,
-                                                    k, ap, recs, out_idx, out_dist, out_robs,
-                                                    out_alpha);
+    const unsigned blocks = (unsigned)((total_q + threads - 1) / threads);
+    k_knn<F64, KMAX><<<blocks, threads, 0, s>>>(job0, jobs, n_jobs, total_q, ap);
 }
 
 template <bool F64>
-void launch_knn_k(const aidw_grid *g, const float *qx, const float *qy, long long nq, int k,
-                  const AlphaParams &ap, QRec *recs, int *out_idx, float *out_dist,
-                  float *out_robs, void *out_alpha, cudaStream_t s)
+void launch_knn_k(const KnnJob &job0, const KnnJob *jobs, int n_jobs, long long total_q,
+                  int kmax, const AlphaParams &ap, int threads, cudaStream_t s)
 {
-    if (k <= 8)
-        launch_knn<F64, 8>(g, qx, qy, nq, k, ap, recs, out_idx, out_dist, out_robs, out_alpha, s);
-    else if (k <= 16)
-        launch_knn<F64, 16>(g, qx, qy, nq, k, ap, recs, out_idx, out_dist, out_robs, out_alpha, s);
+    if (kmax <= 8)
+        launch_knn<F64, 8>(job0, jobs, n_jobs, total_q, ap, threads, s);
+    else if (kmax <= 16)
+        launch_knn<F64, 16>(job0, jobs, n_jobs, total_q, ap, threads, s);
     else
-        launch_knn<F64, 32>(g, qx, qy, nq, k, ap, recs, out_idx, out_dist, out_robs, out_alpha, s);
+        launch_knn<F64, 32>(job0, jobs, n_jobs, total_q, ap, threads, s);
 }
 
 }  // namespace
@@ -268,14 +290,41 @@ aidw_status knn_launch(const aidw_grid *g, const float *qx, const float *qy, lon
                        float *out_dist, float *out_robs, void *out_alpha, cudaStream_t s)
 {
     if (n_query <= 0) return AIDW_OK;
+    KnnJob j;
+    j.g = g->dev;
+    j.pts = g->pts;
+    j.start = g->cell_start;
+    j.qx = qx;
+    j.qy = qy;
+    j.recs = recs;
+    j.out_idx = out_idx;
+    j.out_dist = out_dist;
+    j.out_robs = out_robs;
+    j.out_alpha = out_alpha;
+    j.nq = n_query;
+    j.q_base = 0;
+    j.k = k;
+    j.pad_ = 0;
     const int prof = profile_begin(s);
     if (fp64)
-        launch_knn_k<true>(g, qx, qy, n_query, k, ap, recs, out_idx, out_dist, out_robs,
-                           out_alpha, s);
+        launch_knn_k<true>(j, nullptr, 1, n_query, k, ap, kKnnThreads, s);
     else
-        launch_knn_k<false>(g, qx, qy, n_query, k, ap, recs, out_idx, out_dist, out_robs,
-                            out_alpha, s);
+        launch_knn_k<false>(j, nullptr, 1, n_query, k, ap, kKnnThreads, s);
     profile_end(prof, s, AIDW_STAGE_KNN, 1);
+    return cuda_status(cudaGetLastError());
+}
+
+aidw_status knn_launch_batch(const KnnJob *jobs, int n_jobs, long long total_q, int kmax,
+                             bool fp64, const AlphaParams &ap, int threads, cudaStream_t s)
+{
+    if (total_q <= 0 || n_jobs <= 0) return AIDW_OK;
+    if (threads < 32 || threads > kKnnMaxThreads) threads = kKnnThreads;
+    KnnJob none;
+    memset(&none, 0, sizeof(none));
+    if (fp64)
+        launch_knn_k<true>(none, jobs, n_jobs, total_q, kmax, ap, threads, s);
+    else
+        launch_knn_k<false>(none, jobs, n_jobs, total_q, kmax, ap, threads, s);
     return cuda_status(cudaGetLastError());
 }
 

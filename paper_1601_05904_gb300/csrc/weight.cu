@@ -7,9 +7,12 @@
 // contiguous, equal share of them, so all SMs finish together whatever the
 // query count.  A CTA's share covers the tail of one query tile, whole tiles
 // and the head of another; for each query tile it touches it writes one
-// partial (sum w, sum w z) per query to slot (t + cta) of a scratch array,
+// partial (sum w, sum w z) per query to slot (tile + cta) of a scratch array,
 // and a finalize kernel adds the pieces of each query in CTA order
-// (deterministic, no atomics).
+// (deterministic, no atomics).  Many independent jobs (each its own data and
+// queries) run in the same launch by numbering their units, query tiles and
+// queries one job after the other; a CTA finds the job of a unit by binary
+// search in the job table, so one launch balances jobs of any sizes.
 //
 // Data staging.  Each data tile is one contiguous run of 16-byte points; one
 // elected thread streams it into shared memory with a bulk (TMA) copy that
@@ -30,6 +33,7 @@
 // Float64 path (AIDW_FP64_PLAIN): w = pow(d^2, -alpha/2) in float64, plain
 // float64 sums, same decomposition.
 #include <math.h>
+#include <string.h>
 
 #include <algorithm>
 #include <type_traits>
@@ -44,7 +48,8 @@ namespace {
 constexpr int kDTile = 1024;   // points per shared-memory stage
 static_assert(kDTile == kWeightTile, "weighting tiles are staged whole");
 constexpr int kStages = 3;
-constexpr int kChunk = 32;     // points per plain float32 partial sum
+constexpr int kChunk = 32;     // points per plain float32 partial sum (per lane)
+constexpr int kChunk2 = 2 * kChunk;
 constexpr int kWaitTries = 4000;
 
 template <bool F64>
@@ -55,6 +60,7 @@ struct WCfg<false> {
     static constexpr int kQPT = 4;
     static constexpr int kQTile = kThreads * kQPT;
     static constexpr int kMinBlocks = 2;
+    using Part = float4;
 };
 template <>
 struct WCfg<true> {
@@ -62,6 +68,7 @@ struct WCfg<true> {
     static constexpr int kQPT = 2;
     static constexpr int kQTile = kThreads * kQPT;
     static constexpr int kMinBlocks = 1;
+    using Part = double2;
 };
 
 // First unit of CTA j when U units are split over G CTAs.
@@ -76,55 +83,84 @@ __host__ __device__ __forceinline__ long long sk_owner(long long u, long long U,
 }
 
 struct SKArgs {
-    const Point *pts;  // AoS points (float64 path)
-    const float *wt;   // weighting tiles {-x[], -y[], z[]} (float32 path)
-    long long n_data;
-    long long n_pad;   // points incl. padding (multiple of 32)
-    long long D;       // data tiles
-    const float *qx, *qy;
-    long long nq;
-    long long T;       // query tiles
-    long long U;       // units = T * D
-    long long G;       // CTAs
-    const QRec *recs;
+    WJob job0;          // the job of a single-job launch (jobs == nullptr)
+    const WJob *jobs;   // job table of a batched launch
+    int n_jobs;
+    long long U;        // units of all jobs
+    long long G;        // CTAs
+    long long total_q;  // queries of all jobs
     int *status;
 };
 
-__device__ __forceinline__ void issue_tile(const SKArgs &a, Point *buf, uint64_t *bar, long long u)
+__device__ __forceinline__ WJob job_of_unit(const SKArgs &a, long long u)
 {
-    const long long d = u % a.D;
-    const long long p0 = d * kDTile;
-    const long long cnt = min((long long)kDTile, a.n_pad - p0);
-    mbar_expect_tx(bar, (uint32_t)(cnt * sizeof(Point)));
-    bulk_g2s(buf, a.pts + p0, (uint32_t)(cnt * sizeof(Point)), bar);
+    if (!a.jobs) return a.job0;
+    int lo = 0, hi = a.n_jobs - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (a.jobs[mid].unit_base <= u)
+            lo = mid;
+        else
+            hi = mid - 1;
+    }
+    return a.jobs[lo];
 }
 
-// ---------------------------------------------------------------------------
-// float32 compensated weighting
-// ---------------------------------------------------------------------------
-constexpr int kChunk2 = 2 * kChunk;   // points per plain sum; each lane sums kChunk
-
-// Points of tile d that the float32 kernel processes: the valid ones rounded
-// up to kChunk2 (the tile's padding has weight 0).
-__device__ __forceinline__ int soa_count(const SKArgs &a, long long d)
+__device__ __forceinline__ WJob job_of_query(const SKArgs &a, long long gq)
 {
-    const long long rem = a.n_data - d * kDTile;
+    if (!a.jobs) return a.job0;
+    int lo = 0, hi = a.n_jobs - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (a.jobs[mid].q_base <= gq)
+            lo = mid;
+        else
+            hi = mid - 1;
+    }
+    return a.jobs[lo];
+}
+
+// Points of data tile d that the float32 kernel processes: the valid ones
+// rounded up to kChunk2 (the tile's padding has weight 0).
+__device__ __forceinline__ int soa_count(long long n_data, long long d)
+{
+    const long long rem = n_data - d * kDTile;
     const long long c = (rem + kChunk2 - 1) / kChunk2 * kChunk2;
     return (int)min((long long)kDTile, c);
+}
+
+// Points of data tile d in the float64 kernel's AoS layout.
+__device__ __forceinline__ int aos_count(long long n_pad, long long d)
+{
+    return (int)min((long long)kDTile, n_pad - d * kDTile);
 }
 
 __device__ __forceinline__ void issue_tile_soa(const SKArgs &a, float *buf, uint64_t *bar,
                                                long long u)
 {
-    const long long d = u % a.D;
-    const uint32_t bytes = (uint32_t)soa_count(a, d) * 4u;
-    const float *src = a.wt + d * (3 * kDTile);
+    const WJob J = job_of_unit(a, u);
+    const long long d = (u - J.unit_base) % J.D;
+    const uint32_t bytes = (uint32_t)soa_count(J.n_data, d) * 4u;
+    const float *src = J.wt + d * (3 * kDTile);
     mbar_expect_tx(bar, 3u * bytes);
     bulk_g2s(buf, src, bytes, bar);
     bulk_g2s(buf + kDTile, src + kDTile, bytes, bar);
     bulk_g2s(buf + 2 * kDTile, src + 2 * kDTile, bytes, bar);
 }
 
+__device__ __forceinline__ void issue_tile_aos(const SKArgs &a, Point *buf, uint64_t *bar,
+                                               long long u)
+{
+    const WJob J = job_of_unit(a, u);
+    const long long d = (u - J.unit_base) % J.D;
+    const uint32_t bytes = (uint32_t)aos_count(J.n_pad, d) * (uint32_t)sizeof(Point);
+    mbar_expect_tx(bar, bytes);
+    bulk_g2s(buf, J.pts + d * kDTile, bytes, bar);
+}
+
+// ---------------------------------------------------------------------------
+// float32 compensated weighting
+// ---------------------------------------------------------------------------
 // Each thread holds kQPT queries; every packed instruction applies one query
 // to two consecutive data points (lanes), so a 16-byte shared load of the
 // tile's x (or y, z) array feeds two packed operands.
@@ -137,8 +173,8 @@ __global__ void __launch_bounds__(WCfg<false>::kThreads, WCfg<false>::kMinBlocks
     float *buf = reinterpret_cast<float *>(smem_raw);
     __shared__ __align__(8) uint64_t full[kStages];
 
-    const long long j = blockIdx.x;
-    const long long u0 = sk_begin(j, a.U, a.G), u1 = sk_begin(j + 1, a.U, a.G);
+    const long long cta = blockIdx.x;
+    const long long u0 = sk_begin(cta, a.U, a.G), u1 = sk_begin(cta + 1, a.U, a.G);
     if (u0 >= u1) return;
     if (threadIdx.x == 0) {
         for (int s = 0; s < kStages; ++s) mbar_init(&full[s], 1);
@@ -152,18 +188,19 @@ __global__ void __launch_bounds__(WCfg<false>::kThreads, WCfg<false>::kMinBlocks
     const F2 zero2 = f2_pack(0.0f, 0.0f);
     long long u = u0;
     while (u < u1) {
-        const long long t = u / a.D;
-        const long long seg_end = min(u1, (t + 1) * a.D);
+        const WJob J = job_of_unit(a, u);
+        const long long t = (u - J.unit_base) / J.D;
+        const long long seg_end = min(u1, J.unit_base + (t + 1) * J.D);
 
         F2 qx2[Q], qy2[Q], c2[Q], b2[Q], hw[Q], lw[Q], hz[Q], lz[Q];
 #pragma unroll
         for (int i = 0; i < Q; ++i) {
             const long long q = t * C::kQTile + (long long)i * C::kThreads + threadIdx.x;
             float qx = 0.0f, qy = 0.0f, c = -1.0f, b = 0.0f;
-            if (q < a.nq) {
-                qx = a.qx[q];
-                qy = a.qy[q];
-                const QRec r = a.recs[q];
+            if (q < J.nq) {
+                qx = J.qx[q];
+                qy = J.qy[q];
+                const QRec r = J.recs[q];
                 if (r.n_hit > 0 || !(r.alpha == r.alpha)) {
                     c = 0.0f;  // result replaced in the finalize step
                 } else {
@@ -185,7 +222,7 @@ __global__ void __launch_bounds__(WCfg<false>::kThreads, WCfg<false>::kMinBlocks
             const float *X = buf + s * 3 * kDTile;
             const float *Y = X + kDTile;
             const float *Z = Y + kDTile;
-            const int cnt = soa_count(a, u % a.D);
+            const int cnt = soa_count(J.n_data, (u - J.unit_base) % J.D);
             if (ok) {
                 for (int c0 = 0; c0 < cnt; c0 += kChunk2) {
                     F2 ps[Q], pz[Q];
@@ -208,7 +245,8 @@ __global__ void __launch_bounds__(WCfg<false>::kThreads, WCfg<false>::kMinBlocks
                                 const F2 d2 = f2_fma(dy, dy, f2_mul(dx, dx));
                                 float d0, d1;
                                 f2_unpack(d2, d0, d1);
-                                const F2 tt = f2_fma(f2_pack(lg2_sfu(d0), lg2_sfu(d1)), c2[i], b2[i]);
+                                const F2 tt =
+                                    f2_fma(f2_pack(lg2_sfu(d0), lg2_sfu(d1)), c2[i], b2[i]);
                                 float t0, t1;
                                 f2_unpack(tt, t0, t1);
                                 const F2 w = f2_pack(ex2_sfu(t0), ex2_sfu(t1));
@@ -239,7 +277,7 @@ __global__ void __launch_bounds__(WCfg<false>::kThreads, WCfg<false>::kMinBlocks
                 issue_tile_soa(a, buf + s * 3 * kDTile, &full[s], u + kStages);
         }
 
-        const long long slot = t + j;
+        const long long slot = J.tile_base + t + cta;
 #pragma unroll
         for (int i = 0; i < Q; ++i) {
             float w0, w1, wl0, wl1, z0, z1, zl0, zl1;
@@ -255,14 +293,16 @@ __global__ void __launch_bounds__(WCfg<false>::kThreads, WCfg<false>::kMinBlocks
     }
 }
 
-__global__ void k_finalize_f32(const float4 *__restrict__ part, const QRec *__restrict__ recs,
-                               long long nq, long long D, long long U, long long G,
-                               float *__restrict__ out_z)
+// Adds the pieces of each query's partial sums in CTA order and divides.
+__global__ void k_finalize_f32(SKArgs a, const float4 *__restrict__ part)
 {
     using C = WCfg<false>;
-    const long long q = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    if (q >= nq) return;
-    const QRec r = recs[q];
+    const long long gq = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (gq >= a.total_q) return;
+    const WJob J = job_of_query(a, gq);
+    const long long q = gq - J.q_base;
+    float *out_z = static_cast<float *>(J.out_z);
+    const QRec r = J.recs[q];
     if (!(r.alpha == r.alpha)) {
         out_z[q] = __int_as_float(0x7fc00000);
         return;
@@ -272,10 +312,11 @@ __global__ void k_finalize_f32(const float4 *__restrict__ part, const QRec *__re
         return;
     }
     const long long t = q / C::kQTile, l = q % C::kQTile;
-    const long long j0 = sk_owner(t * D, U, G), j1 = sk_owner((t + 1) * D - 1, U, G);
+    const long long ub = J.unit_base + t * J.D;
+    const long long j0 = sk_owner(ub, a.U, a.G), j1 = sk_owner(ub + J.D - 1, a.U, a.G);
     float hw = 0.0f, lw = 0.0f, hz = 0.0f, lz = 0.0f;
     for (long long j = j0; j <= j1; ++j) {
-        const float4 v = part[(t + j) * C::kQTile + l];
+        const float4 v = part[(J.tile_base + t + j) * C::kQTile + l];
         comp_add(hw, lw, v.x);
         lw = add_rn(lw, v.y);
         comp_add(hz, lz, v.z);
@@ -295,8 +336,8 @@ __global__ void __launch_bounds__(WCfg<true>::kThreads, WCfg<true>::kMinBlocks)
     Point *buf = reinterpret_cast<Point *>(smem_raw);
     __shared__ __align__(8) uint64_t full[kStages];
 
-    const long long j = blockIdx.x;
-    const long long u0 = sk_begin(j, a.U, a.G), u1 = sk_begin(j + 1, a.U, a.G);
+    const long long cta = blockIdx.x;
+    const long long u0 = sk_begin(cta, a.U, a.G), u1 = sk_begin(cta + 1, a.U, a.G);
     if (u0 >= u1) return;
     if (threadIdx.x == 0) {
         for (int s = 0; s < kStages; ++s) mbar_init(&full[s], 1);
@@ -305,12 +346,13 @@ __global__ void __launch_bounds__(WCfg<true>::kThreads, WCfg<true>::kMinBlocks)
     __syncthreads();
     if (threadIdx.x == 0)
         for (int s = 0; s < kStages; ++s)
-            if (u0 + s < u1) issue_tile(a, buf + s * kDTile, &full[s], u0 + s);
+            if (u0 + s < u1) issue_tile_aos(a, buf + s * kDTile, &full[s], u0 + s);
 
     long long u = u0;
     while (u < u1) {
-        const long long t = u / a.D;
-        const long long seg_end = min(u1, (t + 1) * a.D);
+        const WJob J = job_of_unit(a, u);
+        const long long t = (u - J.unit_base) / J.D;
+        const long long seg_end = min(u1, J.unit_base + (t + 1) * J.D);
         float qx[C::kQPT], qy[C::kQPT];
         double e[C::kQPT], sw[C::kQPT], swz[C::kQPT];
 #pragma unroll
@@ -319,10 +361,10 @@ __global__ void __launch_bounds__(WCfg<true>::kThreads, WCfg<true>::kMinBlocks)
             qx[i] = 0.0f;
             qy[i] = 0.0f;
             e[i] = -1.0;
-            if (q < a.nq) {
-                qx[i] = a.qx[q];
-                qy[i] = a.qy[q];
-                const double al = a.recs[q].alpha;
+            if (q < J.nq) {
+                qx[i] = J.qx[q];
+                qy[i] = J.qy[q];
+                const double al = J.recs[q].alpha;
                 if (al == al) e[i] = -0.5 * al;
             }
             sw[i] = swz[i] = 0.0;
@@ -332,7 +374,7 @@ __global__ void __launch_bounds__(WCfg<true>::kThreads, WCfg<true>::kMinBlocks)
             const uint32_t par = (uint32_t)(((u - u0) / kStages) & 1);
             const bool ok = mbar_wait_bounded(&full[s], par, kWaitTries);
             const Point *tile = buf + s * kDTile;
-            const int cnt = (int)min((long long)kDTile, a.n_pad - (u % a.D) * kDTile);
+            const int cnt = aos_count(J.n_pad, (u - J.unit_base) % J.D);
             if (ok) {
                 for (int jj = 0; jj < cnt; ++jj) {
                     const float4 p = reinterpret_cast<const float4 *>(tile)[jj];
@@ -354,9 +396,9 @@ __global__ void __launch_bounds__(WCfg<true>::kThreads, WCfg<true>::kMinBlocks)
                 return;
             }
             if (threadIdx.x == 0 && u + kStages < u1)
-                issue_tile(a, buf + s * kDTile, &full[s], u + kStages);
+                issue_tile_aos(a, buf + s * kDTile, &full[s], u + kStages);
         }
-        const long long slot = t + j;
+        const long long slot = J.tile_base + t + cta;
 #pragma unroll
         for (int i = 0; i < C::kQPT; ++i)
             part[slot * C::kQTile + (long long)i * C::kThreads + threadIdx.x] =
@@ -364,14 +406,15 @@ __global__ void __launch_bounds__(WCfg<true>::kThreads, WCfg<true>::kMinBlocks)
     }
 }
 
-__global__ void k_finalize_f64(const double2 *__restrict__ part, const QRec *__restrict__ recs,
-                               long long nq, long long D, long long U, long long G,
-                               double *__restrict__ out_z)
+__global__ void k_finalize_f64(SKArgs a, const double2 *__restrict__ part)
 {
     using C = WCfg<true>;
-    const long long q = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    if (q >= nq) return;
-    const QRec r = recs[q];
+    const long long gq = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (gq >= a.total_q) return;
+    const WJob J = job_of_query(a, gq);
+    const long long q = gq - J.q_base;
+    double *out_z = static_cast<double *>(J.out_z);
+    const QRec r = J.recs[q];
     if (!(r.alpha == r.alpha)) {
         out_z[q] = r.alpha;
         return;
@@ -381,10 +424,11 @@ __global__ void k_finalize_f64(const double2 *__restrict__ part, const QRec *__r
         return;
     }
     const long long t = q / C::kQTile, l = q % C::kQTile;
-    const long long j0 = sk_owner(t * D, U, G), j1 = sk_owner((t + 1) * D - 1, U, G);
+    const long long ub = J.unit_base + t * J.D;
+    const long long j0 = sk_owner(ub, a.U, a.G), j1 = sk_owner(ub + J.D - 1, a.U, a.G);
     double sw = 0.0, swz = 0.0;
     for (long long j = j0; j <= j1; ++j) {
-        const double2 v = part[(t + j) * C::kQTile + l];
+        const double2 v = part[(J.tile_base + t + j) * C::kQTile + l];
         sw += v.x;
         swz += v.y;
     }
@@ -395,7 +439,8 @@ __global__ void k_finalize_f64(const double2 *__restrict__ part, const QRec *__r
 template <bool F64>
 constexpr size_t stage_smem()
 {
-    return F64 ? (size_t)kStages * kDTile * sizeof(Point) : (size_t)kStages * 3 * kDTile * sizeof(float);
+    return F64 ? (size_t)kStages * kDTile * sizeof(Point)
+               : (size_t)kStages * 3 * kDTile * sizeof(float);
 }
 
 template <bool F64>
@@ -421,51 +466,74 @@ int resident_ctas(int device)
     return c;
 }
 
+// Launches the weighting kernel and the finalize kernel for the jobs in a.
+template <bool F64>
+aidw_status launch(const SKArgs &a, void *part, cudaStream_t s)
+{
+    using C = WCfg<F64>;
+    using Part = typename C::Part;
+    const size_t smem = stage_smem<F64>();
+    int prof = profile_begin(s);
+    if (F64)
+        k_weight_f64<<<(unsigned)a.G, C::kThreads, smem, s>>>(a, static_cast<double2 *>(part));
+    else
+        k_weight_f32<<<(unsigned)a.G, C::kThreads, smem, s>>>(a, static_cast<float4 *>(part));
+    profile_end(prof, s, AIDW_STAGE_WEIGHT, 1);
+    prof = profile_begin(s);
+    const unsigned fb = (unsigned)((a.total_q + 255) / 256);
+    if (F64)
+        k_finalize_f64<<<fb, 256, 0, s>>>(a, static_cast<const double2 *>(part));
+    else
+        k_finalize_f32<<<fb, 256, 0, s>>>(a, static_cast<const float4 *>(part));
+    profile_end(prof, s, AIDW_STAGE_FINALIZE, 1);
+    (void)sizeof(Part);
+    return cuda_status(cudaGetLastError());
+}
+
+// The single job of a grid and one query set.
+template <bool F64>
+SKArgs single_job(const aidw_grid *g, const float *qx, const float *qy, long long nq,
+                  const QRec *recs, void *out_z)
+{
+    using C = WCfg<F64>;
+    SKArgs a;
+    memset(&a, 0, sizeof(a));
+    WJob &J = a.job0;
+    J.wt = g->wt;
+    J.pts = g->pts;
+    J.qx = qx;
+    J.qy = qy;
+    J.recs = recs;
+    J.out_z = out_z;
+    J.n_data = g->n_data;
+    J.n_pad = g->n_pad;
+    J.D = weight_data_tiles(g->n_data, g->n_pad, F64);
+    J.T = (nq + C::kQTile - 1) / C::kQTile;
+    J.nq = nq;
+    a.jobs = nullptr;
+    a.n_jobs = 1;
+    a.U = J.T * J.D;
+    a.total_q = nq;
+    a.status = &g->dev->status;
+    return a;
+}
+
 template <bool F64>
 aidw_status run(const aidw_grid *g, const float *qx, const float *qy, long long nq,
                 const QRec *recs, void *out_z, cudaStream_t s)
 {
     using C = WCfg<F64>;
-    using Part = typename std::conditional<F64, double2, float4>::type;
-    SKArgs a;
-    a.pts = g->pts;
-    a.wt = g->wt;
-    a.n_data = g->n_data;
-    a.n_pad = g->n_pad;
-    a.D = F64 ? (g->n_pad + kDTile - 1) / kDTile : g->n_wtiles;
-    a.qx = qx;
-    a.qy = qy;
-    a.nq = nq;
-    a.T = (nq + C::kQTile - 1) / C::kQTile;
-    a.U = a.T * a.D;
+    SKArgs a = single_job<F64>(g, qx, qy, nq, recs, out_z);
     a.G = std::min<long long>(resident_ctas<F64>(g->device), a.U);
-    a.recs = recs;
-    a.status = &g->dev->status;
-
-    Part *part = nullptr;
-    const size_t part_bytes = sizeof(Part) * (size_t)C::kQTile * (size_t)(a.T + a.G);
-    if (cudaMallocAsync((void **)&part, part_bytes, s) != cudaSuccess) {
+    void *part = nullptr;
+    const size_t part_bytes = sizeof(typename C::Part) * (size_t)C::kQTile * (size_t)(a.job0.T + a.G);
+    if (cudaMallocAsync(&part, part_bytes, s) != cudaSuccess) {
         cudaGetLastError();
         return AIDW_ERR_OOM;
     }
-    const size_t smem = stage_smem<F64>();
-    int prof = profile_begin(s);
-    if (F64)
-        k_weight_f64<<<(unsigned)a.G, C::kThreads, smem, s>>>(a, reinterpret_cast<double2 *>(part));
-    else
-        k_weight_f32<<<(unsigned)a.G, C::kThreads, smem, s>>>(a, reinterpret_cast<float4 *>(part));
-    profile_end(prof, s, AIDW_STAGE_WEIGHT, 1);
-    prof = profile_begin(s);
-    const unsigned fb = (unsigned)((nq + 255) / 256);
-    if (F64)
-        k_finalize_f64<<<fb, 256, 0, s>>>(reinterpret_cast<double2 *>(part), recs, nq, a.D, a.U,
-                                          a.G, static_cast<double *>(out_z));
-    else
-        k_finalize_f32<<<fb, 256, 0, s>>>(reinterpret_cast<float4 *>(part), recs, nq, a.D, a.U,
-                                          a.G, static_cast<float *>(out_z));
-    profile_end(prof, s, AIDW_STAGE_FINALIZE, 1);
+    const aidw_status st = launch<F64>(a, part, s);
     cudaFreeAsync(part, s);
-    return cuda_status(cudaGetLastError());
+    return st;
 }
 
 template <bool F64>
@@ -474,45 +542,36 @@ aidw_status run_scratch(const aidw_grid *g, const float *qx, const float *qy, lo
                         cudaStream_t s)
 {
     using C = WCfg<F64>;
-    using Part = typename std::conditional<F64, double2, float4>::type;
-    SKArgs a;
-    a.pts = g->pts;
-    a.wt = g->wt;
-    a.n_data = g->n_data;
-    a.n_pad = g->n_pad;
-    a.D = F64 ? (g->n_pad + kDTile - 1) / kDTile : g->n_wtiles;
-    a.qx = qx;
-    a.qy = qy;
-    a.nq = nq;
-    a.T = (nq + C::kQTile - 1) / C::kQTile;
-    a.U = a.T * a.D;
-    const long long slot_bytes = (long long)sizeof(Part) * C::kQTile;
-    const long long g_fit = (long long)(scratch_bytes / (size_t)slot_bytes) - a.T;
+    SKArgs a = single_job<F64>(g, qx, qy, nq, recs, out_z);
+    const long long slot_bytes = (long long)sizeof(typename C::Part) * C::kQTile;
+    const long long g_fit = (long long)(scratch_bytes / (size_t)slot_bytes) - a.job0.T;
     if (g_fit < 1) return AIDW_ERR_INVALID_ARG;
     a.G = std::min<long long>(std::min<long long>(resident_ctas<F64>(g->device), a.U), g_fit);
-    a.recs = recs;
-    a.status = &g->dev->status;
-    Part *part = static_cast<Part *>(scratch);
-    const size_t smem = stage_smem<F64>();
-    int prof = profile_begin(s);
-    if (F64)
-        k_weight_f64<<<(unsigned)a.G, C::kThreads, smem, s>>>(a, reinterpret_cast<double2 *>(part));
-    else
-        k_weight_f32<<<(unsigned)a.G, C::kThreads, smem, s>>>(a, reinterpret_cast<float4 *>(part));
-    profile_end(prof, s, AIDW_STAGE_WEIGHT, 1);
-    prof = profile_begin(s);
-    const unsigned fb = (unsigned)((nq + 255) / 256);
-    if (F64)
-        k_finalize_f64<<<fb, 256, 0, s>>>(reinterpret_cast<double2 *>(part), recs, nq, a.D, a.U,
-                                          a.G, static_cast<double *>(out_z));
-    else
-        k_finalize_f32<<<fb, 256, 0, s>>>(reinterpret_cast<float4 *>(part), recs, nq, a.D, a.U,
-                                          a.G, static_cast<float *>(out_z));
-    profile_end(prof, s, AIDW_STAGE_FINALIZE, 1);
-    return cuda_status(cudaGetLastError());
+    return launch<F64>(a, scratch, s);
 }
 
 }  // namespace
+
+long long weight_data_tiles(long long n_data, long long n_pad, bool fp64)
+{
+    return fp64 ? (n_pad + kDTile - 1) / kDTile : (n_data + kDTile - 1) / kDTile;
+}
+
+long long weight_query_tile(bool fp64)
+{
+    return fp64 ? WCfg<true>::kQTile : WCfg<false>::kQTile;
+}
+
+int weight_resident_ctas(int device, bool fp64)
+{
+    return fp64 ? resident_ctas<true>(device) : resident_ctas<false>(device);
+}
+
+size_t weight_partial_bytes(bool fp64)
+{
+    return fp64 ? sizeof(WCfg<true>::Part) * WCfg<true>::kQTile
+                : sizeof(WCfg<false>::Part) * WCfg<false>::kQTile;
+}
 
 aidw_status weight_launch_scratch(const aidw_grid *g, const float *qx, const float *qy,
                                   long long n_query, bool fp64, const QRec *recs, void *out_z,
@@ -530,6 +589,23 @@ aidw_status weight_launch(const aidw_grid *g, const float *qx, const float *qy,
     if (n_query <= 0) return AIDW_OK;
     return fp64 ? run<true>(g, qx, qy, n_query, recs, out_z, s)
                 : run<false>(g, qx, qy, n_query, recs, out_z, s);
+}
+
+aidw_status weight_launch_batch(const WJob *jobs, int n_jobs, long long total_u,
+                                long long total_q, bool fp64, void *part, long long G,
+                                int *status, int device, cudaStream_t s)
+{
+    if (total_u <= 0 || total_q <= 0) return AIDW_OK;
+    SKArgs a;
+    memset(&a, 0, sizeof(a));
+    a.jobs = jobs;
+    a.n_jobs = n_jobs;
+    a.U = total_u;
+    a.G = std::max<long long>(1, std::min<long long>(G, total_u));
+    a.total_q = total_q;
+    a.status = status;
+    (void)device;
+    return fp64 ? launch<true>(a, part, s) : launch<false>(a, part, s);
 }
 
 }  // namespace aidw

@@ -1,0 +1,136 @@
+"""Batched AIDW (many independent jobs in one pass): every job's predictions
+equal the single-job path's and the oracle's, across job sizes, k, graph
+replays with new buffers, the autotuner and error paths."""
+import numpy as np
+import pytest
+
+from gpu_helpers import TOL_FP32, TOL_FP64, dev, host
+from paper_1601_05904_gb300 import inputs
+
+pytestmark = pytest.mark.gpu
+
+
+def _jobs(aidw, spec, seed=0):
+    """spec: list of (n, m, k, clustered_fraction)."""
+    jobs, raw = [], []
+    for j, (n, m, k, frac) in enumerate(spec):
+        rng = np.random.default_rng(seed * 1000 + j)
+        x, y = inputs.mixed_points(rng, n, frac, 4)
+        z = inputs.field_kilo(rng, x, y)
+        qx, qy = inputs.uniform_points(rng, m, 0.0, 1000.0)
+        raw.append((x, y, z, qx, qy, k))
+        jobs.append(aidw.BatchJob(dev(x), dev(y), dev(z), dev(qx), dev(qy), k))
+    return jobs, raw
+
+
+SPEC = [(1, 5, 1, 0.0), (10, 0, 8, 0.0), (33, 100, 8, 0.5), (1000, 1500, 10, 0.3),
+        (4097, 3001, 16, 0.9), (2500, 1024, 24, 0.0), (700, 2049, 32, 0.6),
+        (12000, 5000, 10, 0.8), (64, 64, 17, 0.0), (3000, 1, 12, 0.2)]
+
+
+@pytest.mark.parametrize("fp64", [False, True])
+def test_batch_matches_single_job_and_oracle(aidw, oracle, fp64):
+    prec = aidw.AIDW_FP64_PLAIN if fp64 else aidw.AIDW_FP32_COMP
+    p = aidw.Params(k=10, precision=prec)
+    jobs, raw = _jobs(aidw, SPEC, seed=1)
+    plan = aidw.aidw_batch_plan_create(jobs, p)
+    outs = aidw.aidw_batch_run(plan, jobs)
+    assert aidw.aidw_batch_plan_status(plan) == 0
+    tol = TOL_FP64 if fp64 else TOL_FP32
+    for (x, y, z, qx, qy, k), o in zip(raw, outs):
+        if qx.size == 0:
+            assert o.numel() == 0
+            continue
+        got = host(o).astype(np.float64)
+        ref = oracle.aidw(x, y, z, qx, qy, k)
+        err = oracle.normalized_error(got, ref["z"], ref["scale"])
+        assert err.max() <= tol, err.max()
+        ps = aidw.Params(k=k, precision=prec)
+        g = aidw.aidw_grid_build(dev(x), dev(y), dev(z), ps)
+        single, _ = aidw.aidw_interpolate(g, dev(qx), dev(qy), ps)
+        g.destroy()
+        np.testing.assert_allclose(got, host(single).astype(np.float64), rtol=0,
+                                   atol=(2 * tol) * np.abs(z).max())
+    plan.destroy()
+
+
+def test_graph_replay_with_new_buffers(aidw, oracle):
+    p = aidw.Params(k=10)
+    jobs_a, raw_a = _jobs(aidw, SPEC, seed=2)
+    jobs_b, raw_b = _jobs(aidw, SPEC, seed=3)   # same shapes, other data
+    plan = aidw.aidw_batch_plan_create(jobs_a, p)
+    for jobs, raw in ((jobs_a, raw_a), (jobs_b, raw_b), (jobs_a, raw_a)):
+        for j in jobs:
+            j.out_z = None
+        outs = aidw.aidw_batch_run(plan, jobs)
+        assert aidw.aidw_batch_plan_status(plan) == 0
+        for (x, y, z, qx, qy, k), o in zip(raw, outs):
+            if qx.size:
+                ref = oracle.aidw(x, y, z, qx, qy, k)
+                assert oracle.normalized_error(host(o), ref["z"], ref["scale"]).max() <= TOL_FP32
+    plan.destroy()
+
+
+def test_autotuner_keeps_results(aidw):
+    p = aidw.Params(k=10)
+    jobs, raw = _jobs(aidw, [(20000, 4000, 10, 0.9), (5000, 3000, 24, 0.0)] * 3, seed=4)
+    plan = aidw.aidw_batch_plan_create(jobs, p)
+    before = [host(o).copy() for o in aidw.aidw_batch_run(plan, jobs)]
+    best = aidw.aidw_batch_plan_tune(plan, jobs)
+    info = aidw.aidw_batch_plan_get(plan)
+    assert best > 0 and info["cell_scale"] in (0.75, 1.0, 1.5, 2.0, 3.0)
+    assert info["knn_threads"] in (64, 128, 256)
+    for j in jobs:
+        j.out_z = None
+    after = [host(o) for o in aidw.aidw_batch_run(plan, jobs)]
+    assert aidw.aidw_batch_plan_status(plan) == 0
+    for a, b, r in zip(before, after, raw):
+        np.testing.assert_allclose(a, b, rtol=0, atol=2e-6 * np.abs(r[2]).max())
+    plan.destroy()
+
+
+def test_one_shot_batch(aidw, oracle):
+    jobs, raw = _jobs(aidw, SPEC[:5], seed=5)
+    outs = aidw.aidw_batch(jobs, aidw.Params(k=10))
+    for (x, y, z, qx, qy, k), o in zip(raw, outs):
+        if qx.size:
+            ref = oracle.aidw(x, y, z, qx, qy, k)
+            assert oracle.normalized_error(host(o), ref["z"], ref["scale"]).max() <= TOL_FP32
+
+
+def test_batch_workload_sampled(aidw, oracle):
+    """A slice of the 512-job workload (n_j log-uniform in [1e3, 2e5],
+    k_j in {8,10,16,24,32}, mixed clustering): the first 48 jobs, every job
+    checked on a sample of its queries."""
+    ws = inputs.batch_jobs(n_jobs=48)
+    jobs = [aidw.BatchJob(dev(w.x), dev(w.y), dev(w.z), dev(w.qx), dev(w.qy), w.k) for w in ws]
+    outs = aidw.aidw_batch(jobs, aidw.Params(k=10))
+    for w, o in zip(ws, outs):
+        s = inputs.query_subsample(w.m, 24, seed=w.seed)
+        ref = oracle.aidw(w.x, w.y, w.z, w.qx[s], w.qy[s], w.k)
+        err = oracle.normalized_error(host(o)[s], ref["z"], ref["scale"])
+        assert err.max() <= TOL_FP32, (w.name, err.max())
+
+
+def test_batch_errors(aidw):
+    p = aidw.Params(k=10)
+    jobs, raw = _jobs(aidw, [(100, 10, 10, 0.0), (50, 10, 8, 0.0)], seed=6)
+    plan = aidw.aidw_batch_plan_create(jobs, p)
+    other, _ = _jobs(aidw, [(100, 10, 10, 0.0), (51, 10, 8, 0.0)], seed=6)
+    with pytest.raises(aidw.AidwError) as e:
+        aidw.aidw_batch_run(plan, other)
+    assert e.value.status == 1
+    plan.destroy()
+    bad, _ = _jobs(aidw, [(5, 10, 8, 0.0)], seed=7)
+    with pytest.raises(aidw.AidwError) as e:
+        aidw.aidw_batch_plan_create(bad, p)
+    assert e.value.status == 2
+    # a non-finite data value in one job is reported by the plan status
+    jobs, raw = _jobs(aidw, [(100, 10, 10, 0.0), (200, 10, 10, 0.0)], seed=8)
+    zz = raw[1][2].copy()
+    zz[7] = np.nan
+    jobs[1].z = dev(zz)
+    plan = aidw.aidw_batch_plan_create(jobs, p)
+    aidw.aidw_batch_run(plan, jobs)
+    assert aidw.aidw_batch_plan_status(plan) == 3
+    plan.destroy()
