@@ -176,3 +176,21 @@ def test_pipe_rate_probe(aidw):
     r = aidw.aidw_probe_pipe_rates()
     assert r["lg2"] > 1 and r["ex2"] > 1 and r["ffma2_lanes"] > 1
     assert r["ex2"] >= 0.9 * r["lg2"]
+
+
+@pytest.mark.slow
+def test_precision_form_4M_sampled(aidw, oracle):
+    """n = m = 4,194,304 uniform in [0,1000]^2: float32-compensated path on
+    every query, float64 GPU path on 4096 queries, oracle on samples."""
+    w = inputs.uniform_kilo(n=1 << 22, seed=3)
+    zq, al = _interp(aidw, w.x, w.y, w.z, w.qx, w.qy, 10)
+    s = inputs.query_subsample(w.m, 128)
+    _check(oracle, w.x, w.y, w.z, w.qx[s], w.qy[s], 10, zq[s], al[s], TOL_FP32, 1e-5)
+    s64 = np.arange(4096)
+    z64, a64 = _interp(aidw, w.x, w.y, w.z, w.qx[s64], w.qy[s64], 10, fp64=True)
+    # float64 GPU path against the oracle, and the float32 path against it
+    s2 = np.arange(0, 4096, 64)
+    ref = _check(oracle, w.x, w.y, w.z, w.qx[s2], w.qy[s2], 10, z64[s2], a64[s2], TOL_FP64, 1e-9)
+    assert ref <= TOL_FP64
+    scale = np.abs(w.z).max()
+    np.testing.assert_allclose(zq[s64].astype(np.float64), z64, rtol=0, atol=TOL_FP32 * scale)
