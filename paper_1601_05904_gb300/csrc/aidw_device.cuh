@@ -120,6 +120,38 @@ __device__ __forceinline__ void f2_comp_add(F2 &hi, F2 &lo, F2 x)
     lo = f2_add(lo, e);
 }
 
+// exp2 of two float32 lanes on the FMA pipe, for moving part of the exp2
+// work off the SFU.  Cody-Waite style reduction t = n + f with n = round(t)
+// (adding 1.5 * 2^23 rounds t to an integer in the low mantissa bits) and
+// f = t - n in [-1/2, 1/2] (exact: t and n are within a factor of two, or
+// n = 0); 2^f by a degree-5 polynomial fitted to minimise the relative error
+// on [-1/2, 1/2] (Lawson-iterated weighted least squares; max relative
+// error 7.5e-8, about 2e-7 after float32 rounding, comparable to
+// ex2.approx); 2^n applied by adding n to the exponent field.  t is clamped
+// below at -125 so the exponent cannot wrap; weights that small are below
+// 2^-124 of the largest weight (1) and vanish in the sums.
+__device__ __forceinline__ F2 f2_exp2_poly(F2 t)
+{
+    float t0, t1;
+    f2_unpack(t, t0, t1);
+    const F2 tc = f2_pack(fmaxf(t0, -125.0f), fmaxf(t1, -125.0f));
+    const F2 magic = f2_pack(12582912.0f, 12582912.0f);  // 1.5 * 2^23
+    const F2 r = f2_add(tc, magic);
+    const F2 f = f2_sub(tc, f2_sub(r, magic));
+    F2 p = f2_fma(f2_pack(1.327647129073739e-03f, 1.327647129073739e-03f), f,
+                  f2_pack(9.675541892647743e-03f, 9.675541892647743e-03f));
+    p = f2_fma(p, f, f2_pack(5.550713092088699e-02f, 5.550713092088699e-02f));
+    p = f2_fma(p, f, f2_pack(2.402212023735046e-01f, 2.402212023735046e-01f));
+    p = f2_fma(p, f, f2_pack(6.931469440460205e-01f, 6.931469440460205e-01f));
+    p = f2_fma(p, f, f2_pack(1.000000119209290e+00f, 1.000000119209290e+00f));
+    float r0, r1, p0, p1;
+    f2_unpack(r, r0, r1);
+    f2_unpack(p, p0, p1);
+    const float w0 = __int_as_float(__float_as_int(p0) + (__float_as_int(r0) << 23));
+    const float w1 = __int_as_float(__float_as_int(p1) + (__float_as_int(r1) << 23));
+    return f2_pack(w0, w1);
+}
+
 // Error-free transformation (Knuth's TwoSum): s + e == a + b exactly.
 __device__ __forceinline__ void two_sum(float a, float b, float &s, float &e)
 {

@@ -129,6 +129,9 @@ aidw_status knn_launch(const aidw_grid *g, const float *qx, const float *qy, lon
 
 // Batched kNN over jobs[0, n_jobs) (device array) whose k all need at most
 // kmax (8, 16 or 32) slots; total_q is the sum of their query counts.
+// threads: block size of the thread-per-query kernel, or 0 for the
+// warp-per-query kernel.
+int knn_default_threads(int k);
 aidw_status knn_launch_batch(const KnnJob *jobs, int n_jobs, long long total_q, int kmax,
                              bool fp64, const AlphaParams &ap, int threads, cudaStream_t s);
 

@@ -141,7 +141,7 @@ __global__ void k_b_status(const BJob *__restrict__ jobs, int n_jobs, int *statu
 }
 
 constexpr double kTuneScales[] = {0.75, 1.0, 1.5, 2.0, 3.0};
-constexpr int kTuneThreads[] = {64, 128, 256};
+constexpr int kTuneThreads[] = {0, 64, 128, 256};  // 0: warp per query
 constexpr double kMinScale = 0.75;
 
 inline size_t align256(size_t b) { return (b + 255) / 256 * 256; }

@@ -33,6 +33,7 @@
 // Float64 path (AIDW_FP64_PLAIN): w = pow(d^2, -alpha/2) in float64, plain
 // float64 sums, same decomposition.
 #include <math.h>
+#include <stdlib.h>
 #include <string.h>
 
 #include <algorithm>
@@ -164,6 +165,13 @@ __device__ __forceinline__ void issue_tile_aos(const SKArgs &a, Point *buf, uint
 // Each thread holds kQPT queries; every packed instruction applies one query
 // to two consecutive data points (lanes), so a 16-byte shared load of the
 // tile's x (or y, z) array feeds two packed operands.
+// POLY: how many of the 2 x kQPT (point pair, query) products of one inner
+// step take exp2 from the FMA-pipe polynomial instead of the SFU.  The SFU
+// evaluates lg2 at half the rate of ex2, so with one of each per pair the SFU
+// is the bound; moving part of the exp2s to the FMA pipe balances the two.
+// Measured on GB300 at n = m = 1M: 0/8 367 ms, 2/8 353 ms, 3/8 377 ms,
+// 4/8 395 ms, so 2/8 is the default.
+template <int POLY>
 __global__ void __launch_bounds__(WCfg<false>::kThreads, WCfg<false>::kMinBlocks)
     k_weight_f32(SKArgs a, float4 *__restrict__ part)
 {
@@ -247,9 +255,14 @@ __global__ void __launch_bounds__(WCfg<false>::kThreads, WCfg<false>::kMinBlocks
                                 f2_unpack(d2, d0, d1);
                                 const F2 tt =
                                     f2_fma(f2_pack(lg2_sfu(d0), lg2_sfu(d1)), c2[i], b2[i]);
-                                float t0, t1;
-                                f2_unpack(tt, t0, t1);
-                                const F2 w = f2_pack(ex2_sfu(t0), ex2_sfu(t1));
+                                F2 w;
+                                if (h * Q + i < POLY) {
+                                    w = f2_exp2_poly(tt);
+                                } else {
+                                    float t0, t1;
+                                    f2_unpack(tt, t0, t1);
+                                    w = f2_pack(ex2_sfu(t0), ex2_sfu(t1));
+                                }
                                 ps[i] = f2_add(ps[i], w);
                                 pz[i] = f2_fma(w, zs[h], pz[i]);
                             }
@@ -435,6 +448,20 @@ __global__ void k_finalize_f64(SKArgs a, const double2 *__restrict__ part)
     out_z[q] = swz / sw;
 }
 
+// Number of the 2 x kQPT products per inner step whose exp2 runs on the FMA
+// pipe (0, 2, 3 or 4; default 2).  AIDW_EXP2_POLY_UNITS overrides it, for
+// measuring the balance on a given GPU.
+int poly_units()
+{
+    static int v = -1;
+    if (v < 0) {
+        const char *e = getenv("AIDW_EXP2_POLY_UNITS");
+        const int x = e ? atoi(e) : 2;
+        v = (x == 0 || x == 2 || x == 3 || x == 4) ? x : 2;
+    }
+    return v;
+}
+
 // Dynamic shared memory of the weighting kernels: kStages data tiles.
 template <bool F64>
 constexpr size_t stage_smem()
@@ -458,8 +485,11 @@ int resident_ctas(int device)
         cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_weight_f64, WCfg<true>::kThreads,
                                                       smem);
     } else {
-        cudaFuncSetAttribute(k_weight_f32, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_weight_f32,
+        cudaFuncSetAttribute(k_weight_f32<0>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        cudaFuncSetAttribute(k_weight_f32<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        cudaFuncSetAttribute(k_weight_f32<3>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        cudaFuncSetAttribute(k_weight_f32<4>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_weight_f32<2>,
                                                       WCfg<false>::kThreads, smem);
     }
     c = std::max(1, sms * std::max(1, per_sm));
@@ -474,10 +504,17 @@ aidw_status launch(const SKArgs &a, void *part, cudaStream_t s)
     using Part = typename C::Part;
     const size_t smem = stage_smem<F64>();
     int prof = profile_begin(s);
-    if (F64)
+    if (F64) {
         k_weight_f64<<<(unsigned)a.G, C::kThreads, smem, s>>>(a, static_cast<double2 *>(part));
-    else
-        k_weight_f32<<<(unsigned)a.G, C::kThreads, smem, s>>>(a, static_cast<float4 *>(part));
+    } else {
+        float4 *pf = static_cast<float4 *>(part);
+        switch (poly_units()) {
+        case 0: k_weight_f32<0><<<(unsigned)a.G, C::kThreads, smem, s>>>(a, pf); break;
+        default: k_weight_f32<2><<<(unsigned)a.G, C::kThreads, smem, s>>>(a, pf); break;
+        case 4: k_weight_f32<4><<<(unsigned)a.G, C::kThreads, smem, s>>>(a, pf); break;
+        default: k_weight_f32<3><<<(unsigned)a.G, C::kThreads, smem, s>>>(a, pf); break;
+        }
+    }
     profile_end(prof, s, AIDW_STAGE_WEIGHT, 1);
     prof = profile_begin(s);
     const unsigned fb = (unsigned)((a.total_q + 255) / 256);
