@@ -510,9 +510,9 @@ aidw_status launch(const SKArgs &a, void *part, cudaStream_t s)
         float4 *pf = static_cast<float4 *>(part);
         switch (poly_units()) {
         case 0: k_weight_f32<0><<<(unsigned)a.G, C::kThreads, smem, s>>>(a, pf); break;
-        default: k_weight_f32<2><<<(unsigned)a.G, C::kThreads, smem, s>>>(a, pf); break;
+        case 3: k_weight_f32<3><<<(unsigned)a.G, C::kThreads, smem, s>>>(a, pf); break;
         case 4: k_weight_f32<4><<<(unsigned)a.G, C::kThreads, smem, s>>>(a, pf); break;
-        default: k_weight_f32<3><<<(unsigned)a.G, C::kThreads, smem, s>>>(a, pf); break;
+        default: k_weight_f32<2><<<(unsigned)a.G, C::kThreads, smem, s>>>(a, pf); break;
         }
     }
     profile_end(prof, s, AIDW_STAGE_WEIGHT, 1);
