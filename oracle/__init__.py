@@ -11,6 +11,7 @@ and wraps its functions with numpy marshalling only:
   r_exp / r_obs / R / mu / alpha   Eq. 2, 3, 4, 5, 6
   knn                              Sec. 2.3 brute force (full sort, first k)
   aidw                             Sec. 2.2 steps 1-3 and Eq. 1 (all points)
+  aidw_local                       the same with Eq. 1 over the k nearest points
   grid                             Sec. 3.2.1-3.2.3 even grid, cell order
 """
 from __future__ import annotations
@@ -98,6 +99,10 @@ def _load():
         lib.oracle_aidw.argtypes = [c_f, c_f, c_f, i64, c_f, c_f, i64, ctypes.c_int,
                                     c_d, ctypes.c_double, ctypes.c_double,
                                     ctypes.c_double, c_d, c_d, c_d, c_d, ctypes.c_int]
+        lib.oracle_aidw_local.restype = None
+        lib.oracle_aidw_local.argtypes = [c_f, c_f, c_f, i64, c_f, c_f, i64, ctypes.c_int,
+                                          c_d, ctypes.c_double, ctypes.c_double,
+                                          ctypes.c_double, c_d, c_d, c_d, ctypes.c_int]
         lib.oracle_grid_dims.restype = None
         lib.oracle_grid_dims.argtypes = [c_f, c_f, i64, ctypes.c_double,
                                          ctypes.c_double, ctypes.c_double, c_d]
@@ -187,6 +192,27 @@ def aidw(x, y, z, qx, qy, k: int, levels=DEFAULT_ALPHA, r_min: float = DEFAULT_R
                             _ptr(out["alpha"], ctypes.c_double),
                             _ptr(out["r_obs"], ctypes.c_double),
                             _ptr(out["scale"], ctypes.c_double), int(nthreads))
+    return out
+
+
+def aidw_local(x, y, z, qx, qy, k: int, levels=DEFAULT_ALPHA, r_min: float = DEFAULT_R_MIN,
+               r_max: float = DEFAULT_R_MAX, area: float = 0.0, nthreads: int = 0):
+    """Local AIDW: alpha as in ``aidw``, Eq. 1 over the k nearest points.
+    Returns a dict of float64 arrays [m]: ``z``, ``alpha``, ``scale``."""
+    x, y, z, qx, qy = _f32(x), _f32(y), _f32(z), _f32(qx), _f32(qy)
+    n, m = x.size, qx.size
+    if not (1 <= k <= n):
+        raise ValueError("need 1 <= k <= n")
+    lv = np.ascontiguousarray(levels, dtype=np.float64)
+    out = {key: np.empty(m, dtype=np.float64) for key in ("z", "alpha", "scale")}
+    if m:
+        _load().oracle_aidw_local(_ptr(x, ctypes.c_float), _ptr(y, ctypes.c_float),
+                                  _ptr(z, ctypes.c_float), n,
+                                  _ptr(qx, ctypes.c_float), _ptr(qy, ctypes.c_float), m, int(k),
+                                  _ptr(lv, ctypes.c_double), float(r_min), float(r_max),
+                                  float(area), _ptr(out["z"], ctypes.c_double),
+                                  _ptr(out["alpha"], ctypes.c_double),
+                                  _ptr(out["scale"], ctypes.c_double), int(nthreads))
     return out
 
 

@@ -21,6 +21,7 @@
  *   oracle_knn          Sec. 2.3 brute-force kNN: every distance, full sort,
  *                       first k; ties ordered by the original index
  *   oracle_aidw         Sec. 2.2 steps 1-3 then Eq. 1 over all data points
+ *   oracle_aidw_local   the same with Eq. 1 over the k nearest points only
  *   oracle_grid_dims /
  *   oracle_grid_fill    Sec. 3.2.1-3.2.3 / 4.1.1-4.1.3 even grid: bounding
  *                       box, cell width from Eq. 2, nCol/nRow, cell index
@@ -247,6 +248,71 @@ void oracle_aidw(const float *x, const float *y, const float *z, int64_t n,
             if (out_alpha) out_alpha[q] = a;
             if (out_robs) out_robs[q] = r_obs;
             if (out_scale) out_scale[q] = sq;
+        }
+        free(nn_d);
+        free(nn_idx);
+        free(buf);
+    }
+    (void)nthreads;
+}
+
+/* ---------------------------------------------------------------------- */
+/* Local AIDW: Eq. 1 with n = k, the k nearest data points only.           */
+/* ---------------------------------------------------------------------- */
+/* Eq. 1 reads "n is the total number of data points used in interpolating";
+ * this variant uses the k nearest points of Sec. 2.3's brute force (ties by
+ * index) both for alpha (Eq. 2-6, unchanged) and for the weighted average.
+ * Coincident points among those k give their mean z. */
+void oracle_aidw_local(const float *x, const float *y, const float *z, int64_t n,
+                       const float *qx, const float *qy, int64_t m, int k,
+                       const double alpha_levels[5], double r_min, double r_max,
+                       double area, double *out_z, double *out_alpha, double *out_scale,
+                       int nthreads)
+{
+    if (!(area > 0.0)) {
+        double minx = x[0], maxx = x[0], miny = y[0], maxy = y[0];
+        for (int64_t i = 1; i < n; ++i) {
+            if (x[i] < minx) minx = x[i];
+            if (x[i] > maxx) maxx = x[i];
+            if (y[i] < miny) miny = y[i];
+            if (y[i] > maxy) maxy = y[i];
+        }
+        area = (maxx - minx) * (maxy - miny);
+    }
+    const double r_exp = oracle_r_exp(n, area);
+#ifdef _OPENMP
+    if (nthreads <= 0) nthreads = omp_get_max_threads();
+#pragma omp parallel num_threads(nthreads)
+#endif
+    {
+        oracle_pair *buf = (oracle_pair *)malloc((size_t)n * sizeof(oracle_pair));
+        int32_t *nn_idx = (int32_t *)malloc((size_t)k * sizeof(int32_t));
+        double *nn_d = (double *)malloc((size_t)k * sizeof(double));
+#ifdef _OPENMP
+#pragma omp for schedule(dynamic, 1)
+#endif
+        for (int64_t q = 0; q < m; ++q) {
+            oracle_knn_one(x, y, n, (double)qx[q], (double)qy[q], k, buf, nn_idx, nn_d);
+            const double R = oracle_R(oracle_r_obs(nn_d, k), r_exp);
+            const double a = oracle_alpha(oracle_mu(R, r_min, r_max), alpha_levels);
+            int nhit = 0;
+            double hz = 0.0, ha = 0.0, sw = 0.0, swz = 0.0, swa = 0.0;
+            for (int j = 0; j < k; ++j) {
+                const double zj = (double)z[nn_idx[j]];
+                if (nn_d[j] == 0.0) {
+                    ++nhit;
+                    hz += zj;
+                    ha += fabs(zj);
+                } else {
+                    const double w = pow(nn_d[j], -a);
+                    sw += w;
+                    swz += w * zj;
+                    swa += w * fabs(zj);
+                }
+            }
+            out_z[q] = nhit ? hz / nhit : swz / sw;
+            if (out_alpha) out_alpha[q] = a;
+            if (out_scale) out_scale[q] = nhit ? ha / nhit : swa / sw;
         }
         free(nn_d);
         free(nn_idx);

@@ -302,3 +302,46 @@ def test_grid_degenerate_boxes(oracle):
     g = oracle.grid(np.full(7, 3.0), np.full(7, -2.0))
     assert g["ncol"] == 1 and g["nrow"] == 1
     assert g["perm"].tolist() == list(range(7))
+
+
+# ---- local AIDW (Eq. 1 over the k nearest points) --------------------------------
+
+def _local_cases():
+    with open(GOLDEN) as f:
+        return json.load(f)["local_cases"]
+
+
+@pytest.mark.parametrize("case", _local_cases(), ids=lambda c: c["name"])
+def test_local_hand_derived_cases(oracle, case):
+    out = oracle.aidw_local(case["x"], case["y"], case["z"], case["qx"], case["qy"], case["k"],
+                            levels=case["levels"], r_min=case["r_min"], r_max=case["r_max"])
+    want = [_eval_closed_form(s) for s in case["expected_z"]]
+    np.testing.assert_allclose(out["z"], want, rtol=1e-13)
+
+
+def test_local_with_k_equal_n_is_the_all_points_form(oracle):
+    w = inputs.unit_square(32, m=200, seed=3)
+    a = oracle.aidw(w.x, w.y, w.z, w.qx, w.qy, 32)
+    b = oracle.aidw_local(w.x, w.y, w.z, w.qx, w.qy, 32)
+    np.testing.assert_allclose(b["z"], a["z"], rtol=1e-12)
+    np.testing.assert_array_equal(b["alpha"], a["alpha"])
+
+
+def test_local_alpha_matches_all_points_alpha(oracle):
+    w = _small()
+    a = oracle.aidw(w.x, w.y, w.z, w.qx, w.qy, 10)
+    b = oracle.aidw_local(w.x, w.y, w.z, w.qx, w.qy, 10)
+    np.testing.assert_array_equal(b["alpha"], a["alpha"])
+    # a local average stays within the range of the k neighbours' values
+    idx, _ = oracle.knn(w.x, w.y, w.qx, w.qy, 10)
+    zn = w.z[idx].astype(np.float64)
+    assert (b["z"] >= zn.min(1) - 1e-12).all() and (b["z"] <= zn.max(1) + 1e-12).all()
+
+
+def test_local_constant_field_and_hits(oracle):
+    w = _small()
+    out = oracle.aidw_local(w.x, w.y, np.full(w.n, -1.5, np.float32), w.qx, w.qy, 8)
+    np.testing.assert_allclose(out["z"], -1.5, rtol=1e-14)
+    sel = np.arange(0, w.n, 41)
+    out = oracle.aidw_local(w.x, w.y, w.z, w.x[sel], w.y[sel], 8)
+    np.testing.assert_array_equal(out["z"], w.z[sel].astype(np.float64))
