@@ -50,6 +50,10 @@ def parse():
     ap.add_argument("--workload", choices=("uniform", "clustered", "batch"), default="uniform")
     ap.add_argument("--jobs", type=int, default=512, help="jobs of the batch workload")
     ap.add_argument("--no-tune", action="store_true", help="batch: skip the autotuner")
+    ap.add_argument("--mode", choices=("aidw", "local", "knn-table", "sweep"), default="aidw",
+                    help="aidw: Eq. 1 over all points; local: Eq. 1 over the k nearest; "
+                         "knn-table: grid vs all-points kNN at the paper's sizes; "
+                         "sweep: the full step at the paper's sizes")
     ap.add_argument("--e2e-steps", type=int, default=3)
     ap.add_argument("--fp64-queries", type=int, default=16384)
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
@@ -232,9 +236,12 @@ def run_ours(args):
     out_z = torch.empty(w.m, dtype=torch.float32, device=dev)
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
 
+    interp = (binding.aidw_interpolate_local if args.mode == "local"
+              else binding.aidw_interpolate)
+
     def step():
         g = binding.aidw_grid_build(t["x"], t["y"], t["z"], params)
-        binding.aidw_interpolate(g, t["qx"], t["qy"], params, out_z=out_z)
+        interp(g, t["qx"], t["qy"], params, out_z=out_z)
         g.destroy()
 
     for _ in range(args.warmup):
@@ -279,11 +286,11 @@ def run_ours(args):
         p64 = pkg.Params(k=w.k, precision=binding.AIDW_FP64_PLAIN)
         qx64, qy64 = t["qx"][:mq].contiguous(), t["qy"][:mq].contiguous()
         g = binding.aidw_grid_build(t["x"], t["y"], t["z"], p64)
-        binding.aidw_interpolate(g, qx64, qy64, p64)
+        interp(g, qx64, qy64, p64)
         torch.cuda.synchronize()
         a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         a.record()
-        binding.aidw_interpolate(g, qx64, qy64, p64)
+        interp(g, qx64, qy64, p64)
         b.record()
         torch.cuda.synchronize()
         g.destroy()
@@ -335,11 +342,26 @@ def run_ours(args):
                                f"{pairs_per_sm_clk:.2f} pairs per SM per clock x "
                                f"{props.multi_processor_count} SMs x {sm_max:.0f} MHz max clock"),
                 "pipe_rates_per_sm_clk": rates}
+    if args.mode == "local":
+        # kNN + local weighting in one kernel: algorithmic bytes are the
+        # queries (8 B in, 4 B out) and the data set read once (16 B points
+        # + 4 B z + 4 B cell head per point)
+        k_ms, k_launches = stage["knn"]
+        alg = 12.0 * w.m + 24.0 * w.n
+        hbm = float(peaks.get("hbm_gbs", 6800.0))
+        ach = alg / (k_ms / k_launches / 1000.0) / 1e9 if k_launches else None
+        roofline = {"bound": "hbm", "kernel": "k_knn (grid kNN + local weighting)",
+                    "achieved": ach, "peak": hbm, "unit": "GB/s",
+                    "frac": (ach / hbm) if ach else None, "traffic": None,
+                    "peak_basis": "MEASURED_PEAKS.json hbm_gbs (copy); the kernel is bound by "
+                                  "dependent L2 gathers of the ring search, not by HBM"}
     stages_ms = {k: v[0] / args.steps for k, v in stage.items()}
     cpu = None
     if not args.no_cpu_baseline and world >= 1:
         cpu = cpu_baseline(w, args.cpu_seconds, rank)
-    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+    metric = METRIC if args.mode == "aidw" else \
+        "local AIDW interpolated points/s at n=m=1M (kNN + Eq. 1 over the k nearest)"
+    line = {"metric": metric, "value": value, "unit": UNIT, "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": step_ms,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
             "data": "synthetic", "config": workload_config(args, world),
@@ -422,12 +444,76 @@ def run_batch(args):
     return 0
 
 
+PAPER_SIZES = (10240, 51200, 102400, 512000, 1024000)  # 10K .. 1000K with 1K = 1024
+
+
+def _time_ms(fn, reps):
+    import torch
+    fn()
+    torch.cuda.synchronize()
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a.record()
+    for _ in range(reps):
+        fn()
+    b.record()
+    torch.cuda.synchronize()
+    return a.elapsed_time(b) / reps
+
+
+def run_tables(args):
+    """Per-size tables at the paper's sizes (uniform data = queries in a square)."""
+    import torch
+
+    import paper_1601_05904_gb300 as pkg
+    from paper_1601_05904_gb300 import binding, inputs
+
+    torch.cuda.set_device(0)
+    binding.load()
+    dev = torch.device("cuda", 0)
+    rows = []
+    for n in PAPER_SIZES:
+        w = inputs.uniform_kilo(n=n, k=args.k, seed=1)
+        t = {a: torch.from_numpy(getattr(w, a)).to(dev) for a in ("x", "y", "z", "qx", "qy")}
+        p = pkg.Params(k=w.k)
+        if args.mode == "knn-table":
+            def grid_knn():
+                g = binding.aidw_grid_build(t["x"], t["y"], t["z"], p)
+                binding.aidw_knn(g, t["qx"], t["qy"], w.k, want=("robs",))
+                g.destroy()
+            g = binding.aidw_grid_build(t["x"], t["y"], t["z"], p)
+
+            def brute():
+                binding.aidw_knn_bruteforce(g, t["qx"], t["qy"], w.k, want=("robs",))
+            reps = max(1, args.steps)
+            ms_grid = _time_ms(grid_knn, reps)
+            ms_brute = _time_ms(brute, 1 if n > 200000 else reps)
+            g.destroy()
+            rows.append({"n": n, "grid_build_plus_knn_ms": ms_grid, "all_points_knn_ms": ms_brute,
+                         "speedup": ms_brute / ms_grid})
+        else:
+            def step():
+                g = binding.aidw_grid_build(t["x"], t["y"], t["z"], p)
+                binding.aidw_interpolate(g, t["qx"], t["qy"], p)
+                g.destroy()
+            ms = _time_ms(step, max(1, args.steps if n < 500000 else 2))
+            rows.append({"n": n, "ms": ms, "points_per_s": n / (ms / 1000.0)})
+    metric = ("kNN stage time, grid search vs all-points search (paper Table 3 sizes)"
+              if args.mode == "knn-table" else
+              "AIDW step time at the paper's sizes (paper Table 1 sizes)")
+    print(json.dumps({"metric": metric, "unit": "ms", "k": args.k, "data": "synthetic uniform",
+                      "device": torch.cuda.get_device_properties(dev).name, "rows": rows}),
+          flush=True)
+    return 0
+
+
 def main():
     args = parse()
     if args.impl == "reference":
         return run_reference(args)
     if args.workload == "batch":
         return run_batch(args)
+    if args.mode in ("knn-table", "sweep"):
+        return run_tables(args)
     return run_ours(args)
 
 

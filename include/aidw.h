@@ -241,6 +241,27 @@ aidw_status aidw_interpolate_noalloc(const aidw_grid *g, const float *qx, const 
                                      int64_t n_query, const aidw_params *p, void *out_z,
                                      void *out_alpha, aidw_stream_t stream);
 
+/* The kNN of the authors' earlier GPU AIDW, which the paper improves on
+ * (Sec. 3.1): one thread per query scans every data point and keeps its k
+ * best distances in a sorted list (insertion with neighbour swaps), with the
+ * data points staged through shared memory in tiles.  O(n_query * n_data).
+ * Same outputs, float32 distance and (distance, index) order as aidw_knn, so
+ * the two return identical results; kept as the baseline that measures the
+ * grid search's gain (the paper's Table 3 comparison). */
+aidw_status aidw_knn_bruteforce(const aidw_grid *g, const float *qx, const float *qy,
+                                int64_t n_query, int k, int32_t *out_idx, float *out_dist,
+                                float *out_robs, aidw_stream_t stream);
+
+/* Local AIDW: alpha exactly as aidw_interpolate (Eq. 2-6 from the k nearest
+ * neighbours), but the weighted average of Eq. 1 taken over those k
+ * neighbours only (n = k in Eq. 1's "data points used in interpolating")
+ * instead of all data points.  O(n_query * k) after the kNN search; one
+ * kernel, no scratch.  Coincident neighbours give their mean z.  Outputs as
+ * aidw_interpolate (float32 or float64 by p->precision). */
+aidw_status aidw_interpolate_local(const aidw_grid *g, const float *qx, const float *qy,
+                                   int64_t n_query, const aidw_params *p, void *out_z,
+                                   void *out_alpha, aidw_stream_t stream);
+
 /* Short English name of a status code (static storage). */
 const char *aidw_status_string(aidw_status s);
 

@@ -118,6 +118,10 @@ def load(path: str | None = None):
         lib.aidw_knn.argtypes = [vp, vp, vp, i64, c_int, vp, vp, vp, vp]
         lib.aidw_interpolate.restype = c_int
         lib.aidw_interpolate.argtypes = [vp, vp, vp, i64, P(CParams), vp, vp, vp]
+        lib.aidw_knn_bruteforce.restype = c_int
+        lib.aidw_knn_bruteforce.argtypes = [vp, vp, vp, i64, c_int, vp, vp, vp, vp]
+        lib.aidw_interpolate_local.restype = c_int
+        lib.aidw_interpolate_local.argtypes = [vp, vp, vp, i64, P(CParams), vp, vp, vp]
         lib.aidw_profile_enable.restype = c_int
         lib.aidw_profile_enable.argtypes = [c_int]
         lib.aidw_profile_read.restype = c_int
@@ -257,6 +261,25 @@ def aidw_knn(grid: Grid, qx, qy, k: int, out_idx=None, out_dist=None, out_robs=N
     return out_idx, out_dist, out_robs
 
 
+def aidw_knn_bruteforce(grid: Grid, qx, qy, k: int, out_idx=None, out_dist=None, out_robs=None,
+                        want=("idx", "dist", "robs"), stream=None):
+    """All-points per-thread kNN (the paper's original algorithm); same
+    outputs as aidw_knn."""
+    import torch
+    qx, qy = _f32_dev(qx, "qx"), _f32_dev(qy, "qy")
+    m = qx.numel()
+    if out_idx is None and "idx" in want:
+        out_idx = torch.empty((m, k), dtype=torch.int32, device=qx.device)
+    if out_dist is None and "dist" in want:
+        out_dist = torch.empty((m, k), dtype=torch.float32, device=qx.device)
+    if out_robs is None and "robs" in want:
+        out_robs = torch.empty(m, dtype=torch.float32, device=qx.device)
+    _check(load().aidw_knn_bruteforce(grid.handle, _ptr(qx), _ptr(qy), m, int(k), _ptr(out_idx),
+                                      _ptr(out_dist), _ptr(out_robs), _stream(stream)),
+           "aidw_knn_bruteforce")
+    return out_idx, out_dist, out_robs
+
+
 def aidw_interpolate(grid: Grid, qx, qy, params: Params | None = None, out_z=None,
                      out_alpha=None, want_alpha: bool = False, stream=None):
     """AIDW predictions.  Output dtype is float32 (FP32_COMP) or float64
@@ -279,6 +302,25 @@ def aidw_interpolate(grid: Grid, qx, qy, params: Params | None = None, out_z=Non
     _check(load().aidw_interpolate(grid.handle, _ptr(qx), _ptr(qy), m, ctypes.byref(pc),
                                    _ptr(out_z), _ptr(out_alpha), _stream(stream)),
            "aidw_interpolate")
+    return out_z, out_alpha
+
+
+def aidw_interpolate_local(grid: Grid, qx, qy, params: Params | None = None, out_z=None,
+                           out_alpha=None, want_alpha: bool = False, stream=None):
+    """Local AIDW (Eq. 1 over the k nearest points).  Returns (z, alpha | None)."""
+    import torch
+    p = params or Params()
+    qx, qy = _f32_dev(qx, "qx"), _f32_dev(qy, "qy")
+    m = qx.numel()
+    dt = torch.float64 if p.precision == AIDW_FP64_PLAIN else torch.float32
+    if out_z is None:
+        out_z = torch.empty(m, dtype=dt, device=qx.device)
+    if out_alpha is None and want_alpha:
+        out_alpha = torch.empty(m, dtype=dt, device=qx.device)
+    pc = p.to_c()
+    _check(load().aidw_interpolate_local(grid.handle, _ptr(qx), _ptr(qy), m, ctypes.byref(pc),
+                                         _ptr(out_z), _ptr(out_alpha), _stream(stream)),
+           "aidw_interpolate_local")
     return out_z, out_alpha
 
 

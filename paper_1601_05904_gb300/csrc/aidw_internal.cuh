@@ -59,6 +59,7 @@ struct aidw_grid {
     int *cell_start;             // [cap + 1] head of each cell (int32)
     int *perm;                   // [n_data] original index at each position
     float *wt;                   // [n_wtiles][3][kWeightTile] weighting tiles
+    float *zorig;                // [n_data] z in the caller's order (local AIDW)
     long long n_wtiles;          // ceil(n_data / kWeightTile)
     long long n_data;
     long long n_pad;             // n_data rounded up (padding points at +inf)
@@ -102,6 +103,8 @@ struct KnnJob {
     float *out_dist;
     float *out_robs;
     void *out_alpha;
+    const float *zorig;  // z by original index (local AIDW)
+    void *out_zlocal;    // local AIDW prediction (Eq. 1 over the k nearest); or null
     long long nq;
     long long q_base;
     int k;
@@ -122,10 +125,18 @@ struct WJob {
     long long unit_base, tile_base, q_base;
 };
 
-// kNN (+ alpha): fills recs (if not null) and the optional public outputs.
+// kNN (+ alpha): fills recs (if not null) and the optional public outputs;
+// out_zlocal (if not null) receives the local AIDW prediction.
 aidw_status knn_launch(const aidw_grid *g, const float *qx, const float *qy, long long n_query,
                        int k, bool fp64, const AlphaParams &ap, QRec *recs, int *out_idx,
-                       float *out_dist, float *out_robs, void *out_alpha, cudaStream_t s);
+                       float *out_dist, float *out_robs, void *out_alpha, cudaStream_t s,
+                       void *out_zlocal = nullptr);
+
+// Brute-force kNN over all data points of the grid (the paper's original
+// per-thread algorithm, kept as a baseline).
+aidw_status knn_launch_brute(const aidw_grid *g, const float *qx, const float *qy,
+                             long long n_query, int k, int *out_idx, float *out_dist,
+                             float *out_robs, cudaStream_t s);
 
 // Batched kNN over jobs[0, n_jobs) (device array) whose k all need at most
 // kmax (8, 16 or 32) slots; total_q is the sum of their query counts.

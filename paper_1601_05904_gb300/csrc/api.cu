@@ -196,6 +196,9 @@ aidw_status aidw_grid_build(const float *x, const float *y, const float *z, int6
     g->n_wtiles = (n_data + kWeightTile - 1) / kWeightTile;
     if (e == cudaSuccess)
         e = cudaMalloc((void **)&g->wt, sizeof(float) * 3 * kWeightTile * (size_t)g->n_wtiles);
+    if (e == cudaSuccess) e = cudaMalloc((void **)&g->zorig, sizeof(float) * (size_t)n_data);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(g->zorig, z, sizeof(float) * (size_t)n_data, cudaMemcpyDeviceToDevice, s);
     if (e != cudaSuccess) {
         cudaGetLastError();
         aidw_grid_destroy(g);
@@ -241,6 +244,7 @@ aidw_status aidw_grid_destroy(aidw_grid *g)
         // drain all work that may still read the grid
         st = aidw_grid_status(g);
     }
+    if (g->zorig) cudaFree(g->zorig);
     if (g->wt) cudaFree(g->wt);
     if (g->perm) cudaFree(g->perm);
     if (g->cell_start) cudaFree(g->cell_start);
@@ -327,6 +331,33 @@ aidw_status aidw_interpolate(const aidw_grid *g, const float *qx, const float *q
     if (st == AIDW_OK) st = weight_launch(g, qx, qy, n_query, fp64, recs, out_z, s);
     cudaFreeAsync(recs, s);
     return st;
+}
+
+aidw_status aidw_knn_bruteforce(const aidw_grid *g, const float *qx, const float *qy,
+                                int64_t n_query, int k, int32_t *out_idx, float *out_dist,
+                                float *out_robs, aidw_stream_t stream)
+{
+    if (!g || n_query < 0 || n_query > kMaxPoints) return AIDW_ERR_INVALID_ARG;
+    if (k < 1 || k > AIDW_MAX_K || k > g->n_data) return AIDW_ERR_K_RANGE;
+    if (n_query == 0) return AIDW_OK;
+    if (!qx || !qy) return AIDW_ERR_INVALID_ARG;
+    return knn_launch_brute(g, qx, qy, n_query, k, out_idx, out_dist, out_robs,
+                            reinterpret_cast<cudaStream_t>(stream));
+}
+
+aidw_status aidw_interpolate_local(const aidw_grid *g, const float *qx, const float *qy,
+                                   int64_t n_query, const aidw_params *p, void *out_z,
+                                   void *out_alpha, aidw_stream_t stream)
+{
+    if (!g || n_query < 0 || n_query > kMaxPoints) return AIDW_ERR_INVALID_ARG;
+    const aidw_status ps = check_params(p, true);
+    if (ps != AIDW_OK) return ps;
+    if (p->k > g->n_data) return AIDW_ERR_K_RANGE;
+    if (n_query == 0) return AIDW_OK;
+    if (!qx || !qy || !out_z) return AIDW_ERR_INVALID_ARG;
+    return knn_launch(g, qx, qy, n_query, p->k, p->precision == AIDW_FP64_PLAIN,
+                      alpha_params(p), nullptr, nullptr, nullptr, nullptr, out_alpha,
+                      reinterpret_cast<cudaStream_t>(stream), out_z);
 }
 
 aidw_status aidw_profile_enable(int on)

@@ -119,6 +119,12 @@ __global__ void __launch_bounds__(kKnnMaxThreads)
             else
                 static_cast<float *>(out_alpha)[q] = __int_as_float(0x7fc00000);
         }
+        if (J.out_zlocal) {
+            if (F64)
+                static_cast<double *>(J.out_zlocal)[q] = nanv;
+            else
+                static_cast<float *>(J.out_zlocal)[q] = __int_as_float(0x7fc00000);
+        }
         return;
     }
 
@@ -261,6 +267,35 @@ __global__ void __launch_bounds__(kKnnMaxThreads)
             static_cast<double *>(out_alpha)[q] = alpha;
         else
             static_cast<float *>(out_alpha)[q] = (float)alpha;
+    }
+    if (J.out_zlocal) {
+        // Eq. 1 over the k neighbours: weights (d^2 / d1^2)^(-alpha/2) (float32
+        // path, SFU, largest weight 1) or pow(d^2, -alpha/2) (float64 path),
+        // sums in float64; coincident neighbours give their mean z.
+        const float c = (float)(-0.5 * alpha);
+        const float b = F64 ? 0.0f : -c * lg2_sfu((float)kd[0]);
+        double sw = 0.0, swz = 0.0, hz = 0.0;
+        int nh = 0;
+#pragma unroll
+        for (int j = 0; j < KMAX; ++j) {
+            if (j < k) {
+                const double zj = (double)J.zorig[ki[j]];
+                if (kd[j] == (D)0) {
+                    ++nh;
+                    hz += zj;
+                } else {
+                    const double w = F64 ? pow((double)kd[j], -0.5 * alpha)
+                                         : (double)ex2_sfu(fma_rn(lg2_sfu((float)kd[j]), c, b));
+                    sw += w;
+                    swz += w * zj;
+                }
+            }
+        }
+        const double zl = nh ? hz / (double)nh : swz / sw;
+        if (F64)
+            static_cast<double *>(J.out_zlocal)[q] = zl;
+        else
+            static_cast<float *>(J.out_zlocal)[q] = (float)zl;
     }
 }
 
@@ -443,6 +478,83 @@ __global__ void __launch_bounds__(kKnnMaxThreads)
     }
 }
 
+// The kNN of the authors' earlier GPU AIDW (Sec. 3.1, the "original"
+// algorithm the paper improves on): every query thread scans ALL data points
+// and keeps its k best in a sorted register list.  Data points are staged
+// through shared memory in tiles of kBruteTile (the "tiled" form).  Same
+// float32 distance and (d^2, index) order as k_knn, so the result is the
+// same; kept as the baseline of the grid search.
+constexpr int kBruteTile = 1024;
+constexpr int kBruteThreads = 256;
+
+template <int KMAX>
+__global__ void __launch_bounds__(kBruteThreads)
+    k_knn_brute(const Point *__restrict__ pts, long long n, const float *__restrict__ qxa,
+                const float *__restrict__ qya, long long nq, int k, int *__restrict__ out_idx,
+                float *__restrict__ out_dist, float *__restrict__ out_robs)
+{
+    __shared__ float4 tile[kBruteTile];
+    const long long q = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    const bool active = q < nq;
+    const float qx = active ? qxa[q] : 0.0f, qy = active ? qya[q] : 0.0f;
+    float kd[KMAX];
+    int ki[KMAX];
+#pragma unroll
+    for (int j = 0; j < KMAX; ++j) {
+        kd[j] = __int_as_float(0x7f800000);
+        ki[j] = 0x7fffffff;
+    }
+    float kth = __int_as_float(0x7f800000);
+    int kthi = 0x7fffffff;
+    for (long long base = 0; base < n; base += kBruteTile) {
+        const int cnt = (int)min((long long)kBruteTile, n - base);
+        __syncthreads();
+        for (int i = threadIdx.x; i < cnt; i += blockDim.x)
+            tile[i] = reinterpret_cast<const float4 *>(pts)[base + i];
+        __syncthreads();
+        if (!active) continue;
+        for (int j = 0; j < cnt; ++j) {
+            const float4 p = tile[j];
+            const int pidx = __float_as_int(p.w);
+            const float d2 = dist2_f32(qx, qy, p.x, p.y);
+            if (d2 < kth || (d2 == kth && pidx < kthi)) {
+                float cd = d2;
+                int ci = pidx;
+#pragma unroll
+                for (int t = 0; t < KMAX; ++t) {
+                    const bool lt = (t < k) && (cd < kd[t] || (cd == kd[t] && ci < ki[t]));
+                    const float td = kd[t];
+                    const int ti = ki[t];
+                    kd[t] = lt ? cd : td;
+                    ki[t] = lt ? ci : ti;
+                    cd = lt ? td : cd;
+                    ci = lt ? ti : ci;
+                }
+                kth = kd[0];
+                kthi = ki[0];
+#pragma unroll
+                for (int t = 1; t < KMAX; ++t) {
+                    if (t == k - 1) {
+                        kth = kd[t];
+                        kthi = ki[t];
+                    }
+                }
+            }
+        }
+    }
+    if (!active) return;
+    double r_obs = 0.0;
+#pragma unroll
+    for (int j = 0; j < KMAX; ++j) {
+        if (j < k) {
+            r_obs += sqrt((double)kd[j]);
+            if (out_idx) out_idx[q * k + j] = ki[j];
+            if (out_dist) out_dist[q * k + j] = sqrtf(kd[j]);
+        }
+    }
+    if (out_robs) out_robs[q] = (float)(r_obs / (double)k);
+}
+
 template <bool F64, int KMAX>
 void launch_knn(const KnnJob &job0, const KnnJob *jobs, int n_jobs, long long total_q,
                 const AlphaParams &ap, int threads, cudaStream_t s)
@@ -489,7 +601,8 @@ int knn_default_threads(int k)
 
 aidw_status knn_launch(const aidw_grid *g, const float *qx, const float *qy, long long n_query,
                        int k, bool fp64, const AlphaParams &ap, QRec *recs, int *out_idx,
-                       float *out_dist, float *out_robs, void *out_alpha, cudaStream_t s)
+                       float *out_dist, float *out_robs, void *out_alpha, cudaStream_t s,
+                       void *out_zlocal)
 {
     if (n_query <= 0) return AIDW_OK;
     KnnJob j;
@@ -503,16 +616,38 @@ aidw_status knn_launch(const aidw_grid *g, const float *qx, const float *qy, lon
     j.out_dist = out_dist;
     j.out_robs = out_robs;
     j.out_alpha = out_alpha;
+    j.zorig = g->zorig;
+    j.out_zlocal = out_zlocal;
     j.nq = n_query;
     j.q_base = 0;
     j.k = k;
     j.pad_ = 0;
-    const int threads = knn_default_threads(k);
+    const int threads = out_zlocal ? kKnnThreads : knn_default_threads(k);
     const int prof = profile_begin(s);
     if (fp64)
         launch_knn_k<true>(j, nullptr, 1, n_query, k, ap, threads, s);
     else
         launch_knn_k<false>(j, nullptr, 1, n_query, k, ap, threads, s);
+    profile_end(prof, s, AIDW_STAGE_KNN, 1);
+    return cuda_status(cudaGetLastError());
+}
+
+aidw_status knn_launch_brute(const aidw_grid *g, const float *qx, const float *qy,
+                             long long n_query, int k, int *out_idx, float *out_dist,
+                             float *out_robs, cudaStream_t s)
+{
+    if (n_query <= 0) return AIDW_OK;
+    const unsigned blocks = (unsigned)((n_query + kBruteThreads - 1) / kBruteThreads);
+    const int prof = profile_begin(s);
+    if (k <= 8)
+        k_knn_brute<8><<<blocks, kBruteThreads, 0, s>>>(g->pts, g->n_data, qx, qy, n_query, k,
+                                                        out_idx, out_dist, out_robs);
+    else if (k <= 16)
+        k_knn_brute<16><<<blocks, kBruteThreads, 0, s>>>(g->pts, g->n_data, qx, qy, n_query, k,
+                                                         out_idx, out_dist, out_robs);
+    else
+        k_knn_brute<32><<<blocks, kBruteThreads, 0, s>>>(g->pts, g->n_data, qx, qy, n_query, k,
+                                                         out_idx, out_dist, out_robs);
     profile_end(prof, s, AIDW_STAGE_KNN, 1);
     return cuda_status(cudaGetLastError());
 }

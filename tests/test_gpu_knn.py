@@ -111,3 +111,19 @@ def test_knn_full_size_sampled(aidw, oracle):
     idx, dist, robs = _knn(aidw, w.x, w.y, w.qx, w.qy, 10, 0.0 or 1.0)
     s = inputs.query_subsample(w.m, 256)
     check_knn(oracle, w.x, w.y, w.qx[s], w.qy[s], 10, idx[s], dist[s], robs[s])
+
+
+@pytest.mark.parametrize("k", [1, 10, 16, 32])
+def test_bruteforce_knn_equals_grid_knn(aidw, oracle, k):
+    """The paper's original all-points kNN and the grid kNN use the same
+    float32 distance and (d^2, index) order: identical results."""
+    w = inputs.clustered_kilo(n=30000, m=3000, seed=41)
+    g = aidw.aidw_grid_build(dev(w.x), dev(w.y), dev(w.z), aidw.Params(cell_scale=1.0))
+    a = [host(t) for t in aidw.aidw_knn(g, dev(w.qx), dev(w.qy), k)]
+    b = [host(t) for t in aidw.aidw_knn_bruteforce(g, dev(w.qx), dev(w.qy), k)]
+    g.destroy()
+    np.testing.assert_array_equal(b[0], a[0])
+    np.testing.assert_array_equal(b[1], a[1])
+    np.testing.assert_array_equal(b[2], a[2])
+    s = np.arange(0, w.m, 7)
+    check_knn(oracle, w.x, w.y, w.qx[s], w.qy[s], k, b[0][s], b[1][s], b[2][s])
