@@ -19,8 +19,10 @@
  *    call enqueues nothing.  Errors the device finds (non-finite input
  *    coordinates, an expired bounded wait) are latched in the grid and
  *    returned by aidw_grid_status() and aidw_grid_destroy().
- *  - The library owns grid handles and per-call scratch, which it takes with
- *    cudaMallocAsync on `stream` and returns the same way.
+ *  - The library owns grid handles and per-call scratch, which it takes in
+ *    stream order on `stream` from a memory pool of its own (one per device)
+ *    and returns the same way; freed blocks stay in that pool for reuse
+ *    until the process exits.
  */
 #ifndef AIDW_H_
 #define AIDW_H_

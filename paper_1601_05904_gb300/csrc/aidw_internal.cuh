@@ -74,6 +74,10 @@ namespace aidw {
 
 // ---- launch helpers (defined in api.cu) -----------------------------------
 aidw_status cuda_status(cudaError_t e);
+// Stream-ordered device allocation from the library's own memory pool on the
+// current device (freed memory stays in the pool for reuse).
+cudaError_t lib_alloc(void **p, size_t bytes, cudaStream_t s);
+void lib_free(void *p, cudaStream_t s);
 // Stage timing: begin returns a handle (-1 when timing is off); end records
 // the closing event and the number of kernels the stage launched.
 int profile_begin(cudaStream_t s);

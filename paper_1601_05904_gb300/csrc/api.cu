@@ -19,6 +19,59 @@ aidw_status cuda_status(cudaError_t e)
     return AIDW_ERR_CUDA;
 }
 
+// ---- memory pool ---------------------------------------------------------------
+// One stream-ordered pool per device, private to the library, that keeps
+// freed blocks (release threshold unbounded): grids and per-call scratch
+// come from it, so repeated builds and calls reuse memory without a
+// cudaMalloc (which can synchronise the device) after the first use.
+namespace api_detail {
+std::mutex g_pool_mu;
+cudaMemPool_t g_pools[64] = {};
+
+cudaMemPool_t pool_for(int device)
+{
+    std::lock_guard<std::mutex> lk(g_pool_mu);
+    if (device < 0 || device >= 64) return nullptr;
+    if (!g_pools[device]) {
+        cudaMemPoolProps props;
+        memset(&props, 0, sizeof(props));
+        props.allocType = cudaMemAllocationTypePinned;
+        props.location.type = cudaMemLocationTypeDevice;
+        props.location.id = device;
+        cudaMemPool_t pool = nullptr;
+        if (cudaMemPoolCreate(&pool, &props) != cudaSuccess) {
+            cudaGetLastError();
+            return nullptr;
+        }
+        uint64_t keep = ~0ull;
+        cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &keep);
+        g_pools[device] = pool;
+    }
+    return g_pools[device];
+}
+}  // namespace api_detail
+
+cudaError_t lib_alloc(void **p, size_t bytes, cudaStream_t s)
+{
+    *p = nullptr;
+    int device = 0;
+    cudaError_t e = cudaGetDevice(&device);
+    if (e != cudaSuccess) return e;
+    cudaMemPool_t pool = api_detail::pool_for(device);
+    e = pool ? cudaMallocFromPoolAsync(p, bytes > 0 ? bytes : 1, pool, s)
+             : cudaMallocAsync(p, bytes > 0 ? bytes : 1, s);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        *p = nullptr;
+    }
+    return e;
+}
+
+void lib_free(void *p, cudaStream_t s)
+{
+    if (p) cudaFreeAsync(p, s);
+}
+
 // ---- stage timing ------------------------------------------------------------
 namespace api_detail {
 
@@ -188,15 +241,15 @@ aidw_status aidw_grid_build(const float *x, const float *y, const float *z, int6
     g->cap_cells = grid_cells_capacity(n_data, g->cell_scale);
     g->stream = s;
 
-    cudaError_t e = cudaMalloc((void **)&g->dev, sizeof(GridDev));
-    if (e == cudaSuccess) e = cudaMalloc((void **)&g->pts, sizeof(Point) * (size_t)g->n_pad);
+    cudaError_t e = lib_alloc((void **)&g->dev, sizeof(GridDev), s);
+    if (e == cudaSuccess) e = lib_alloc((void **)&g->pts, sizeof(Point) * (size_t)g->n_pad, s);
     if (e == cudaSuccess)
-        e = cudaMalloc((void **)&g->cell_start, sizeof(int) * (size_t)(g->cap_cells + 1));
-    if (e == cudaSuccess) e = cudaMalloc((void **)&g->perm, sizeof(int) * (size_t)n_data);
+        e = lib_alloc((void **)&g->cell_start, sizeof(int) * (size_t)(g->cap_cells + 1), s);
+    if (e == cudaSuccess) e = lib_alloc((void **)&g->perm, sizeof(int) * (size_t)n_data, s);
     g->n_wtiles = (n_data + kWeightTile - 1) / kWeightTile;
     if (e == cudaSuccess)
-        e = cudaMalloc((void **)&g->wt, sizeof(float) * 3 * kWeightTile * (size_t)g->n_wtiles);
-    if (e == cudaSuccess) e = cudaMalloc((void **)&g->zorig, sizeof(float) * (size_t)n_data);
+        e = lib_alloc((void **)&g->wt, sizeof(float) * 3 * kWeightTile * (size_t)g->n_wtiles, s);
+    if (e == cudaSuccess) e = lib_alloc((void **)&g->zorig, sizeof(float) * (size_t)n_data, s);
     if (e == cudaSuccess)
         e = cudaMemcpyAsync(g->zorig, z, sizeof(float) * (size_t)n_data, cudaMemcpyDeviceToDevice, s);
     if (e != cudaSuccess) {
@@ -244,12 +297,13 @@ aidw_status aidw_grid_destroy(aidw_grid *g)
         // drain all work that may still read the grid
         st = aidw_grid_status(g);
     }
-    if (g->zorig) cudaFree(g->zorig);
-    if (g->wt) cudaFree(g->wt);
-    if (g->perm) cudaFree(g->perm);
-    if (g->cell_start) cudaFree(g->cell_start);
-    if (g->pts) cudaFree(g->pts);
-    if (g->dev) cudaFree(g->dev);
+    // the device is idle (drained above); return the buffers to the pool
+    lib_free(g->zorig, nullptr);
+    lib_free(g->wt, nullptr);
+    lib_free(g->perm, nullptr);
+    lib_free(g->cell_start, nullptr);
+    lib_free(g->pts, nullptr);
+    lib_free(g->dev, nullptr);
     delete g;
     return st;
 }
@@ -322,14 +376,12 @@ aidw_status aidw_interpolate(const aidw_grid *g, const float *qx, const float *q
     cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
     const bool fp64 = p->precision == AIDW_FP64_PLAIN;
     QRec *recs = nullptr;
-    if (cudaMallocAsync((void **)&recs, sizeof(QRec) * (size_t)n_query, s) != cudaSuccess) {
-        cudaGetLastError();
+    if (lib_alloc((void **)&recs, sizeof(QRec) * (size_t)n_query, s) != cudaSuccess)
         return AIDW_ERR_OOM;
-    }
     aidw_status st = knn_launch(g, qx, qy, n_query, p->k, fp64, alpha_params(p), recs, nullptr,
                                 nullptr, nullptr, out_alpha, s);
     if (st == AIDW_OK) st = weight_launch(g, qx, qy, n_query, fp64, recs, out_z, s);
-    cudaFreeAsync(recs, s);
+    lib_free(recs, s);
     return st;
 }
 

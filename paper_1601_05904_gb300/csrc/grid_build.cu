@@ -127,15 +127,14 @@ aidw_status grid_build_launch(aidw_grid *g, const float *x, const float *y, cons
     int *key = nullptr, *rank = nullptr, *tmp = nullptr, *bsum = nullptr;
     const long long scan_len = cap + 1;
     const long long nb = (scan_len + kScanChunk - 1) / kScanChunk;
-    cudaError_t e = cudaMallocAsync((void **)&key, sizeof(int) * n, s);
-    if (e == cudaSuccess) e = cudaMallocAsync((void **)&rank, sizeof(int) * n, s);
-    if (e == cudaSuccess) e = cudaMallocAsync((void **)&tmp, sizeof(int) * n, s);
-    if (e == cudaSuccess) e = cudaMallocAsync((void **)&bsum, sizeof(int) * nb, s);
+    cudaError_t e = lib_alloc((void **)&key, sizeof(int) * n, s);
+    if (e == cudaSuccess) e = lib_alloc((void **)&rank, sizeof(int) * n, s);
+    if (e == cudaSuccess) e = lib_alloc((void **)&tmp, sizeof(int) * n, s);
+    if (e == cudaSuccess) e = lib_alloc((void **)&bsum, sizeof(int) * nb, s);
     if (e != cudaSuccess) {
-        if (key) cudaFreeAsync(key, s);
-        if (rank) cudaFreeAsync(rank, s);
-        if (tmp) cudaFreeAsync(tmp, s);
-        cudaGetLastError();
+        lib_free(key, s);
+        lib_free(rank, s);
+        lib_free(tmp, s);
         return AIDW_ERR_OOM;
     }
     int *start = g->cell_start;
@@ -169,10 +168,10 @@ aidw_status grid_build_launch(aidw_grid *g, const float *x, const float *y, cons
                                                                     n_wpad);
         ++nl;
     }
-    cudaFreeAsync(key, s);
-    cudaFreeAsync(rank, s);
-    cudaFreeAsync(tmp, s);
-    cudaFreeAsync(bsum, s);
+    lib_free(key, s);
+    lib_free(rank, s);
+    lib_free(tmp, s);
+    lib_free(bsum, s);
     profile_end(prof, s, AIDW_STAGE_GRID_BUILD, nl);
     return cuda_status(cudaGetLastError());
 }

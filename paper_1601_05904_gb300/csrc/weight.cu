@@ -55,6 +55,8 @@ constexpr int kWaitTries = 4000;
 
 template <bool F64>
 struct WCfg;
+// float32: 256 threads x 4 queries at 128 registers (2 CTAs per SM).  512 x 2
+// at 64 registers (twice the warps) measured 360 vs 353 ms at n = m = 1M.
 template <>
 struct WCfg<false> {
     static constexpr int kThreads = 256;
@@ -171,12 +173,13 @@ __device__ __forceinline__ void issue_tile_aos(const SKArgs &a, Point *buf, uint
 // is the bound; moving part of the exp2s to the FMA pipe balances the two.
 // Measured on GB300 at n = m = 1M: 0/8 367 ms, 2/8 353 ms, 3/8 377 ms,
 // 4/8 395 ms, so 2/8 is the default.
-template <int POLY>
-__global__ void __launch_bounds__(WCfg<false>::kThreads, WCfg<false>::kMinBlocks)
+template <int POLY, int THREADS = WCfg<false>::kThreads, int Q = WCfg<false>::kQPT,
+          int MINB = WCfg<false>::kMinBlocks>
+__global__ void __launch_bounds__(THREADS, MINB)
     k_weight_f32(SKArgs a, float4 *__restrict__ part)
 {
     using C = WCfg<false>;
-    constexpr int Q = C::kQPT;
+    static_assert(THREADS * Q == C::kQTile, "a query tile is THREADS x Q queries");
     extern __shared__ __align__(128) unsigned char smem_raw[];
     float *buf = reinterpret_cast<float *>(smem_raw);
     __shared__ __align__(8) uint64_t full[kStages];
@@ -203,7 +206,7 @@ __global__ void __launch_bounds__(WCfg<false>::kThreads, WCfg<false>::kMinBlocks
         F2 qx2[Q], qy2[Q], c2[Q], b2[Q], hw[Q], lw[Q], hz[Q], lz[Q];
 #pragma unroll
         for (int i = 0; i < Q; ++i) {
-            const long long q = t * C::kQTile + (long long)i * C::kThreads + threadIdx.x;
+            const long long q = t * C::kQTile + (long long)i * THREADS + threadIdx.x;
             float qx = 0.0f, qy = 0.0f, c = -1.0f, b = 0.0f;
             if (q < J.nq) {
                 qx = J.qx[q];
@@ -300,7 +303,7 @@ __global__ void __launch_bounds__(WCfg<false>::kThreads, WCfg<false>::kMinBlocks
             f2_unpack(lz[i], zl0, zl1);
             comp_add(w0, wl0, w1);
             comp_add(z0, zl0, z1);
-            part[slot * C::kQTile + (long long)i * C::kThreads + threadIdx.x] =
+            part[slot * C::kQTile + (long long)i * THREADS + threadIdx.x] =
                 make_float4(w0, add_rn(wl0, wl1), z0, add_rn(zl0, zl1));
         }
     }
@@ -564,12 +567,9 @@ aidw_status run(const aidw_grid *g, const float *qx, const float *qy, long long 
     a.G = std::min<long long>(resident_ctas<F64>(g->device), a.U);
     void *part = nullptr;
     const size_t part_bytes = sizeof(typename C::Part) * (size_t)C::kQTile * (size_t)(a.job0.T + a.G);
-    if (cudaMallocAsync(&part, part_bytes, s) != cudaSuccess) {
-        cudaGetLastError();
-        return AIDW_ERR_OOM;
-    }
+    if (lib_alloc(&part, part_bytes, s) != cudaSuccess) return AIDW_ERR_OOM;
     const aidw_status st = launch<F64>(a, part, s);
-    cudaFreeAsync(part, s);
+    lib_free(part, s);
     return st;
 }
 
