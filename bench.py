@@ -50,6 +50,8 @@ def parse():
     ap.add_argument("--workload", choices=("uniform", "clustered", "batch"), default="uniform")
     ap.add_argument("--jobs", type=int, default=512, help="jobs of the batch workload")
     ap.add_argument("--no-tune", action="store_true", help="batch: skip the autotuner")
+    ap.add_argument("--cell-scale", type=float, default=0.0,
+                    help="grid cell width / r_exp (<= 0: the library's choice)")
     ap.add_argument("--mode", choices=("aidw", "local", "knn-table", "sweep"), default="aidw",
                     help="aidw: Eq. 1 over all points; local: Eq. 1 over the k nearest; "
                          "knn-table: grid vs all-points kNN at the paper's sizes; "
@@ -231,7 +233,7 @@ def run_ours(args):
     binding.load()
 
     w = make_workload(args, rank)
-    params = pkg.Params(k=w.k, cell_scale=0.0)
+    params = pkg.Params(k=w.k, cell_scale=args.cell_scale)
     t = {k: torch.from_numpy(getattr(w, k)).to(dev) for k in ("x", "y", "z", "qx", "qy")}
     out_z = torch.empty(w.m, dtype=torch.float32, device=dev)
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)

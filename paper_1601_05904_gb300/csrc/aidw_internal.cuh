@@ -109,6 +109,7 @@ struct KnnJob {
     void *out_alpha;
     const float *zorig;  // z by original index (local AIDW)
     void *out_zlocal;    // local AIDW prediction (Eq. 1 over the k nearest); or null
+    const int *order;    // queries in grid-cell order (thread i takes order[i]); or null
     long long nq;
     long long q_base;
     int k;
@@ -130,11 +131,12 @@ struct WJob {
 };
 
 // kNN (+ alpha): fills recs (if not null) and the optional public outputs;
-// out_zlocal (if not null) receives the local AIDW prediction.
+// out_zlocal (if not null) receives the local AIDW prediction.  sort allows
+// visiting the queries in grid-cell order (takes pool memory).
 aidw_status knn_launch(const aidw_grid *g, const float *qx, const float *qy, long long n_query,
                        int k, bool fp64, const AlphaParams &ap, QRec *recs, int *out_idx,
                        float *out_dist, float *out_robs, void *out_alpha, cudaStream_t s,
-                       void *out_zlocal = nullptr);
+                       void *out_zlocal = nullptr, bool sort = true);
 
 // Brute-force kNN over all data points of the grid (the paper's original
 // per-thread algorithm, kept as a baseline).

@@ -31,6 +31,7 @@
 
 #include "aidw_device.cuh"
 #include "aidw_internal.cuh"
+#include "grid_device.cuh"
 
 namespace aidw {
 
@@ -85,7 +86,7 @@ __global__ void __launch_bounds__(kKnnMaxThreads)
     if (gq >= total_q) return;
     // single-job launches pass the job by value and no table
     const KnnJob J = jobs ? jobs[knn_job_of(jobs, n_jobs, gq)] : job0;
-    const long long q = gq - J.q_base;
+    const long long q = J.order ? (long long)J.order[gq - J.q_base] : gq - J.q_base;
     const GridDev *__restrict__ g = J.g;
     const Point *__restrict__ pts = J.pts;
     const int *__restrict__ start = J.start;
@@ -316,7 +317,7 @@ __global__ void __launch_bounds__(kKnnMaxThreads)
     const long long gq = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     if (gq >= total_q) return;  // uniform across the warp
     const KnnJob J = jobs ? jobs[knn_job_of(jobs, n_jobs, gq)] : job0;
-    const long long q = gq - J.q_base;
+    const long long q = J.order ? (long long)J.order[gq - J.q_base] : gq - J.q_base;
     const GridDev *__restrict__ g = J.g;
     const Point *__restrict__ pts = J.pts;
     const int *__restrict__ start = J.start;
@@ -581,6 +582,104 @@ void launch_knn_k(const KnnJob &job0, const KnnJob *jobs, int n_jobs, long long 
         launch_knn<F64, 32>(job0, jobs, n_jobs, total_q, ap, threads, s);
 }
 
+// ---- queries in grid-cell order ----------------------------------------------
+// Random query order mixes queries from dense clusters and sparse background
+// in one warp, which then runs as long as its slowest query.  Visiting the
+// queries by grid cell (a counting sort over the data grid's cells) gives
+// each warp neighbouring queries with similar ring counts and shared cells.
+// The order changes no result: every query is computed independently.
+__global__ void __launch_bounds__(gridk::kThreads)
+    k_qkeys(const float *__restrict__ qx, const float *__restrict__ qy, long long nq,
+            const GridDev *__restrict__ g, int *__restrict__ count, int *__restrict__ key,
+            int *__restrict__ rank)
+{
+    const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= nq) return;
+    float x = qx[i], y = qy[i];
+    if (!isfinite(x) || !isfinite(y)) x = y = 0.0f;  // flagged by the kNN kernel
+    const double minx = g->min_x, miny = g->min_y, cw = g->cw;
+    const long long nc = g->n_col, nr = g->n_row;
+    long long col = (long long)floor(((double)x - minx) / cw);
+    long long row = (long long)floor(((double)y - miny) / cw);
+    col = col < 0 ? 0 : (col > nc - 1 ? nc - 1 : col);
+    row = row < 0 ? 0 : (row > nr - 1 ? nr - 1 : row);
+    const int c = (int)(row * nc + col);
+    key[i] = c;
+    rank[i] = atomicAdd(count + c, 1);
+}
+
+__global__ void __launch_bounds__(gridk::kThreads) k_qscan_reduce(const int *a, long long len,
+                                                                   int *bsum)
+{
+    gridk::scan_reduce_chunk(a, len, blockIdx.x, bsum + blockIdx.x);
+}
+__global__ void __launch_bounds__(gridk::kThreads) k_qscan_sums(int *bsum, int nb)
+{
+    gridk::scan_sums(bsum, nb);
+}
+__global__ void __launch_bounds__(gridk::kThreads) k_qscan_apply(int *a, long long len,
+                                                                  const int *bsum)
+{
+    gridk::scan_apply_chunk(a, len, blockIdx.x, bsum[blockIdx.x]);
+}
+__global__ void __launch_bounds__(gridk::kThreads)
+    k_qscatter(long long nq, const int *__restrict__ start, const int *__restrict__ key,
+               const int *__restrict__ rank, int *__restrict__ order)
+{
+    const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < nq) order[start[key[i]] + rank[i]] = (int)i;
+}
+
+// Whether the single-grid kNN sorts its queries by cell (AIDW_KNN_SORT=0|1
+// overrides; default on from 4096 queries).
+bool knn_sort_queries(long long nq)
+{
+    static int v = -2;
+    if (v == -2) {
+        const char *e = getenv("AIDW_KNN_SORT");
+        v = e ? (atoi(e) != 0 ? 1 : 0) : -1;
+    }
+    return v >= 0 ? v == 1 : nq >= 4096;
+}
+
+// Fills *order (pool memory, freed by the caller with lib_free) with the
+// queries in cell order; the temporaries are returned to the pool.
+aidw_status query_order(const aidw_grid *g, const float *qx, const float *qy, long long nq,
+                        int **order, cudaStream_t s, int *launches)
+{
+    using namespace gridk;
+    const long long len = g->cap_cells + 1;
+    const long long nb = (len + kScanChunk - 1) / kScanChunk;
+    int *count = nullptr, *key = nullptr, *rank = nullptr, *bsum = nullptr;
+    *order = nullptr;
+    cudaError_t e = lib_alloc((void **)&count, sizeof(int) * len, s);
+    if (e == cudaSuccess) e = lib_alloc((void **)&key, sizeof(int) * nq, s);
+    if (e == cudaSuccess) e = lib_alloc((void **)&rank, sizeof(int) * nq, s);
+    if (e == cudaSuccess) e = lib_alloc((void **)&bsum, sizeof(int) * nb, s);
+    if (e == cudaSuccess) e = lib_alloc((void **)order, sizeof(int) * nq, s);
+    if (e == cudaSuccess) {
+        const unsigned qb = (unsigned)((nq + kThreads - 1) / kThreads);
+        cudaMemsetAsync(count, 0, sizeof(int) * len, s);
+        k_qkeys<<<qb, kThreads, 0, s>>>(qx, qy, nq, g->dev, count, key, rank);
+        k_qscan_reduce<<<(unsigned)nb, kThreads, 0, s>>>(count, len, bsum);
+        k_qscan_sums<<<1, kThreads, 0, s>>>(bsum, (int)nb);
+        k_qscan_apply<<<(unsigned)nb, kThreads, 0, s>>>(count, len, bsum);
+        k_qscatter<<<qb, kThreads, 0, s>>>(nq, count, key, rank, *order);
+        *launches += 5;
+        e = cudaGetLastError();
+    }
+    lib_free(count, s);
+    lib_free(key, s);
+    lib_free(rank, s);
+    lib_free(bsum, s);
+    if (e != cudaSuccess) {
+        lib_free(*order, s);
+        *order = nullptr;
+        return e == cudaErrorMemoryAllocation ? AIDW_ERR_OOM : cuda_status(e);
+    }
+    return AIDW_OK;
+}
+
 }  // namespace
 
 // Launch shape of the single-grid kNN: thread per query (block size) or warp
@@ -602,7 +701,7 @@ int knn_default_threads(int k)
 aidw_status knn_launch(const aidw_grid *g, const float *qx, const float *qy, long long n_query,
                        int k, bool fp64, const AlphaParams &ap, QRec *recs, int *out_idx,
                        float *out_dist, float *out_robs, void *out_alpha, cudaStream_t s,
-                       void *out_zlocal)
+                       void *out_zlocal, bool sort)
 {
     if (n_query <= 0) return AIDW_OK;
     KnnJob j;
@@ -618,17 +717,26 @@ aidw_status knn_launch(const aidw_grid *g, const float *qx, const float *qy, lon
     j.out_alpha = out_alpha;
     j.zorig = g->zorig;
     j.out_zlocal = out_zlocal;
+    j.order = nullptr;
     j.nq = n_query;
     j.q_base = 0;
     j.k = k;
     j.pad_ = 0;
     const int threads = out_zlocal ? kKnnThreads : knn_default_threads(k);
     const int prof = profile_begin(s);
+    int launches = 1;
+    int *order = nullptr;
+    if (sort && knn_sort_queries(n_query)) {
+        const aidw_status st = query_order(g, qx, qy, n_query, &order, s, &launches);
+        if (st != AIDW_OK) return st;
+        j.order = order;
+    }
     if (fp64)
         launch_knn_k<true>(j, nullptr, 1, n_query, k, ap, threads, s);
     else
         launch_knn_k<false>(j, nullptr, 1, n_query, k, ap, threads, s);
-    profile_end(prof, s, AIDW_STAGE_KNN, 1);
+    profile_end(prof, s, AIDW_STAGE_KNN, launches);
+    lib_free(order, s);
     return cuda_status(cudaGetLastError());
 }
 

@@ -68,7 +68,7 @@ extern "C" aidw_status aidw_interpolate_noalloc(const aidw_grid *g, const float 
     cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
     const bool fp64 = p->precision == AIDW_FP64_PLAIN;
     st = knn_launch(g, qx, qy, n_query, p->k, fp64, api_detail::alpha_params(p), recs, nullptr,
-                    nullptr, nullptr, out_alpha, s);
+                    nullptr, nullptr, out_alpha, s, nullptr, false);
     if (st == AIDW_OK)
         st = weight_launch_scratch(g, qx, qy, n_query, fp64, recs, out_z, part, part_bytes, s);
     return st;

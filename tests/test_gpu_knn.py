@@ -127,3 +127,19 @@ def test_bruteforce_knn_equals_grid_knn(aidw, oracle, k):
     np.testing.assert_array_equal(b[2], a[2])
     s = np.arange(0, w.m, 7)
     check_knn(oracle, w.x, w.y, w.qx[s], w.qy[s], k, b[0][s], b[1][s], b[2][s])
+
+
+def test_query_cell_order_changes_nothing(aidw):
+    """From 4096 queries the kNN visits queries in grid-cell order; the same
+    queries below that size run in input order.  Results are identical."""
+    w = inputs.clustered_kilo(n=50000, m=6000, seed=43)
+    g = aidw.aidw_grid_build(dev(w.x), dev(w.y), dev(w.z), aidw.Params(cell_scale=1.0))
+    big = [host(t) for t in aidw.aidw_knn(g, dev(w.qx), dev(w.qy), 20)]
+    small = [host(t) for t in aidw.aidw_knn(g, dev(w.qx[:3000]), dev(w.qy[:3000]), 20)]
+    for a, b in zip(big, small):
+        np.testing.assert_array_equal(a[:3000], b)
+    p = aidw.Params(k=20)
+    zb, ab = aidw.aidw_interpolate(g, dev(w.qx), dev(w.qy), p, want_alpha=True)
+    zs, as_ = aidw.aidw_interpolate(g, dev(w.qx[:3000]), dev(w.qy[:3000]), p, want_alpha=True)
+    np.testing.assert_array_equal(host(ab)[:3000], host(as_))
+    g.destroy()
