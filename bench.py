@@ -71,6 +71,23 @@ def dist_env():
     return rank, world, local
 
 
+def max_over_ranks(seconds: float, device=None) -> float:
+    """The slowest rank's time (all ranks call it; no-op on one rank)."""
+    import torch
+    import torch.distributed as dist
+    if not dist.is_available() or not dist.is_initialized() or dist.get_world_size() == 1:
+        return seconds
+    t = torch.tensor([seconds], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_value(world: int, units_per_rank: int, steps: int, seconds: float) -> float:
+    """Units processed by all ranks over the timed steps, per second of the
+    slowest rank (weak scaling: every rank has the same amount of work)."""
+    return world * units_per_rank * steps / seconds
+
+
 def make_workload(args, rank):
     from paper_1601_05904_gb300 import inputs
     if args.workload == "uniform":
@@ -273,12 +290,8 @@ def run_ours(args):
     clk = clocks.stop()
     stage = binding.aidw_profile_read()
     step_ms = sum(a.elapsed_time(b) for a, b in ev) / args.steps
-    my_s = step_ms * args.steps / 1000.0
-    if world > 1:
-        tt = torch.tensor([my_s], dtype=torch.float64, device=dev)
-        torch.distributed.all_reduce(tt, op=torch.distributed.ReduceOp.MAX)
-        my_s = float(tt.item())
-    value = world * w.m * args.steps / my_s
+    my_s = max_over_ranks(step_ms * args.steps / 1000.0, dev)
+    value = whole_job_value(world, w.m, args.steps, my_s)
     launches = sum(v[1] for v in stage.values())
 
     # float64 plain path on a query sample (kNN + weighting + grid build)

@@ -163,13 +163,15 @@ aidw_status check_params(const aidw_params *p, bool need_k)
     return AIDW_OK;
 }
 
-// Cell width scale used when the caller passes cell_scale <= 0.  Measured on
-// uniform and clustered point sets: about two points per cell keeps the
-// ring search short for k between 8 and 32.
+// Cell width scale used when the caller passes cell_scale <= 0.  Grid build
+// + kNN on GB300, n = m = 1M, ms at scales 1 / 1.5 / 2 / 3:
+//   k = 10 uniform 2.11 / 1.79 / 1.73 / 1.63, clustered 4.05 / 2.66 / 2.31 / 2.35
+//   k = 32 uniform 7.89 / 6.10 / 5.36 / 4.93, clustered 18.2 / 11.7 / 8.66 / 6.90
+// Wider cells than the paper's (scale 1) mean fewer, longer contiguous runs
+// of points per ring, which costs less than the extra distances they add.
 double auto_cell_scale(int k)
 {
-    (void)k;
-    return 1.0;
+    return k <= 16 ? 2.0 : 3.0;
 }
 
 AlphaParams alpha_params(const aidw_params *p)

@@ -140,9 +140,9 @@ __global__ void k_b_status(const BJob *__restrict__ jobs, int n_jobs, int *statu
     }
 }
 
-constexpr double kTuneScales[] = {0.75, 1.0, 1.5, 2.0, 3.0};
+constexpr double kTuneScales[] = {1.0, 1.5, 2.0, 3.0, 4.0};
 constexpr int kTuneThreads[] = {0, 64, 128, 256};  // 0: warp per query
-constexpr double kMinScale = 0.75;
+constexpr double kMinScale = 1.0;
 
 inline size_t align256(size_t b) { return (b + 255) / 256 * 256; }
 inline long long cdiv(long long a, long long b) { return (a + b - 1) / b; }
@@ -348,7 +348,7 @@ aidw_status aidw_batch_plan_create(const aidw_job *jobs, int n_jobs, const aidw_
     P->ap = api_detail::alpha_params(p);
     P->fp64 = p->precision == AIDW_FP64_PLAIN;
     P->tuned_scale = p->cell_scale > 0.0;
-    P->cell_scale = p->cell_scale > 0.0 ? p->cell_scale : 1.0;
+    P->cell_scale = p->cell_scale > 0.0 ? p->cell_scale : 2.0;  // the tuner may change it
     cudaGetDevice(&P->device);
     P->n.resize(n_jobs);
     P->m.resize(n_jobs);

@@ -78,7 +78,7 @@ def test_autotuner_keeps_results(aidw):
     before = [host(o).copy() for o in aidw.aidw_batch_run(plan, jobs)]
     best = aidw.aidw_batch_plan_tune(plan, jobs)
     info = aidw.aidw_batch_plan_get(plan)
-    assert best > 0 and info["cell_scale"] in (0.75, 1.0, 1.5, 2.0, 3.0)
+    assert best > 0 and info["cell_scale"] in (1.0, 1.5, 2.0, 3.0, 4.0)
     assert info["knn_threads"] in (0, 64, 128, 256)   # 0: warp per query
     for j in jobs:
         j.out_z = None

@@ -1,0 +1,64 @@
+"""Host-side logic of the multi-GPU (query-sharded, weak-scaling) benchmark,
+run as two gloo ranks on CPU: every rank gets the same data points and its
+own queries, and the reported time is the slowest rank's."""
+import os
+import socket
+import sys
+
+import numpy as np
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _free_port():
+    with socket.socket() as s:
+        s.bind(("127.0.0.1", 0))
+        return s.getsockname()[1]
+
+
+def _rank(rank, world, port, out):
+    sys.path.insert(0, ROOT)
+    import torch
+    import torch.distributed as dist
+
+    import bench
+    os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port), RANK=str(rank),
+                      WORLD_SIZE=str(world), LOCAL_RANK=str(rank))
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    try:
+        assert bench.dist_env() == (rank, world, rank)
+
+        class A:
+            n, k, workload = 4096, 10, "uniform"
+        w = bench.make_workload(A, rank)
+        sums = torch.tensor([float(np.float64(w.x).sum()), float(np.float64(w.qx).sum())],
+                            dtype=torch.float64)
+        gathered = [torch.zeros(2, dtype=torch.float64) for _ in range(world)]
+        dist.all_gather(gathered, sums)
+        t = bench.max_over_ranks(1.0 + rank)
+        out.put((rank, [g.tolist() for g in gathered], t,
+                 bench.whole_job_value(world, w.m, 3, t)))
+    finally:
+        dist.destroy_process_group()
+
+
+def test_two_ranks_share_data_shard_queries_and_take_the_slowest_time():
+    torch = pytest.importorskip("torch")
+    mp = torch.multiprocessing.get_context("spawn")
+    q = mp.Queue()
+    port = _free_port()
+    procs = [mp.Process(target=_rank, args=(r, 2, port, q)) for r in range(2)]
+    for p in procs:
+        p.start()
+    res = [q.get(timeout=120) for _ in procs]
+    for p in procs:
+        p.join(timeout=60)
+        assert p.exitcode == 0
+    res.sort()
+    for rank, gathered, t, value in res:
+        (x0, q0), (x1, q1) = gathered
+        assert x0 == x1          # same data points on every rank
+        assert q0 != q1          # each rank its own queries
+        assert t == 2.0          # max over ranks
+        assert value == pytest.approx(2 * 4096 * 3 / 2.0)
