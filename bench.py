@@ -349,9 +349,11 @@ def run_ours(args):
     rates = binding.aidw_probe_pipe_rates()
     pairs_per_sm_clk = 1.0 / (1.0 / rates["lg2"] + 1.0 / rates["ex2"])
     peak = pairs_per_sm_clk * props.multi_processor_count * sm_max * 1e6 / 1e9
+    traffic = WEIGHT_DRAM_BYTES_PER_POINT * w.n if w.n == w.m else None
     roofline = {"bound": "alu", "kernel": "k_weight_f32 (all-points weighting, Eq. 1)",
                 "achieved": achieved, "peak": peak, "unit": "Gpair/s",
-                "frac": (achieved / peak) if achieved else None, "traffic": None,
+                "frac": (achieved / peak) if achieved else None, "traffic": traffic,
+                "traffic_basis": "dram bytes per launch, ncu at n = m = 131072 scaled by n",
                 "peak_basis": (f"SFU pipe: measured lg2 {rates['lg2']:.2f} and ex2 "
                                f"{rates['ex2']:.2f} per SM per clock -> "
                                f"{pairs_per_sm_clk:.2f} pairs per SM per clock x "
@@ -460,6 +462,11 @@ def run_batch(args):
 
 
 PAPER_SIZES = (10240, 51200, 102400, 512000, 1024000)  # 10K .. 1000K with 1K = 1024
+
+# DRAM bytes (read + write) of one k_weight_f32 launch per data point, from
+# the ncu capture at n = m = 131,072 (5.80 MB read, 0 written); every input
+# (points, queries, kNN records) is read once, so it scales with n = m.
+WEIGHT_DRAM_BYTES_PER_POINT = 5.800192e6 / 131072
 
 
 def _time_ms(fn, reps):
