@@ -1,0 +1,117 @@
+"""Edge cases of the GPU path against the oracle: queries far outside the
+data, large or negative coordinates, a zero-area (collinear) data set,
+extreme alpha levels, single queries and points, non-default streams and
+several live grids."""
+import numpy as np
+import pytest
+
+from gpu_helpers import TOL_FP32, TOL_FP64, check_knn, dev, host
+from paper_1601_05904_gb300 import inputs
+
+pytestmark = pytest.mark.gpu
+
+
+def _run(aidw, x, y, z, qx, qy, k, fp64=False, stream=None, **kw):
+    p = aidw.Params(k=k, precision=aidw.AIDW_FP64_PLAIN if fp64 else aidw.AIDW_FP32_COMP, **kw)
+    g = aidw.aidw_grid_build(dev(x), dev(y), dev(z), p, stream=stream)
+    zq, al = aidw.aidw_interpolate(g, dev(qx), dev(qy), p, want_alpha=True, stream=stream)
+    if stream is not None:
+        stream.synchronize()
+    out = host(zq).astype(np.float64), host(al).astype(np.float64)
+    assert aidw.aidw_grid_status(g) == 0
+    g.destroy()
+    return out
+
+
+def _check(oracle, x, y, z, qx, qy, k, zq, al, fp64=False, **kw):
+    ref = oracle.aidw(x, y, z, qx, qy, k, **kw)
+    err = oracle.normalized_error(zq, ref["z"], ref["scale"])
+    assert err.max() <= (TOL_FP64 if fp64 else TOL_FP32), err.max()
+    np.testing.assert_allclose(al, ref["alpha"], atol=1e-9 if fp64 else 1e-5)
+
+
+@pytest.mark.parametrize("fp64", [False, True])
+def test_queries_far_outside_the_data(aidw, oracle, fp64):
+    w = inputs.clustered_kilo(n=5000, m=10, seed=51)
+    rng = np.random.default_rng(51)
+    ang = rng.uniform(0, 2 * np.pi, 300)
+    r = rng.uniform(1500, 20000, 300)
+    qx = (500 + r * np.cos(ang)).astype(np.float32)
+    qy = (500 + r * np.sin(ang)).astype(np.float32)
+    zq, al = _run(aidw, w.x, w.y, w.z, qx, qy, 10, fp64)
+    _check(oracle, w.x, w.y, w.z, qx, qy, 10, zq, al, fp64)
+
+
+@pytest.mark.parametrize("offset", [-3.0e5, 1.0e6])
+def test_large_and_negative_coordinates(aidw, oracle, offset):
+    rng = np.random.default_rng(52)
+    x, y = inputs.uniform_points(rng, 8000, offset, offset + 1000.0)
+    z = inputs.field_kilo(rng, x, y)
+    qx, qy = inputs.uniform_points(rng, 1500, offset, offset + 1000.0)
+    for fp64 in (False, True):
+        zq, al = _run(aidw, x, y, z, qx, qy, 10, fp64)
+        _check(oracle, x, y, z, qx, qy, 10, zq, al, fp64)
+    g = aidw.aidw_grid_build(dev(x), dev(y), dev(z), aidw.Params())
+    idx, dist, robs = aidw.aidw_knn(g, dev(qx), dev(qy), 12)
+    g.destroy()
+    check_knn(oracle, x, y, qx, qy, 12, host(idx), host(dist), host(robs))
+
+
+def test_collinear_data_zero_area(aidw, oracle):
+    rng = np.random.default_rng(53)
+    y = rng.uniform(0, 100, 3000).astype(np.float32)
+    x = np.full_like(y, 7.0)
+    z = inputs.field_kilo(rng, x, y)
+    qx = rng.uniform(-10, 20, 500).astype(np.float32)
+    qy = rng.uniform(-10, 110, 500).astype(np.float32)
+    for fp64 in (False, True):
+        zq, al = _run(aidw, x, y, z, qx, qy, 8, fp64)
+        _check(oracle, x, y, z, qx, qy, 8, zq, al, fp64)
+        # r_exp = 0 (zero area): R = inf, mu = 1, alpha = alpha_5
+        np.testing.assert_array_equal(al, 5.0)
+
+
+@pytest.mark.parametrize("levels", [(0.1, 0.2, 0.3, 0.4, 0.5), (6, 7, 8, 9, 10)])
+def test_extreme_alpha_levels(aidw, oracle, levels):
+    w = inputs.uniform_kilo(n=6000, m=1500, seed=54)
+    for fp64 in (False, True):
+        zq, al = _run(aidw, w.x, w.y, w.z, w.qx, w.qy, 10, fp64, alpha=levels)
+        _check(oracle, w.x, w.y, w.z, w.qx, w.qy, 10, zq, al, fp64, levels=levels)
+
+
+def test_single_query_single_point_and_k1(aidw, oracle):
+    w = inputs.unit_square(3000, m=1, seed=55)
+    for k in (1, 32):
+        zq, al = _run(aidw, w.x, w.y, w.z, w.qx, w.qy, k)
+        _check(oracle, w.x, w.y, w.z, w.qx, w.qy, k, zq, al)
+    zq, _ = _run(aidw, w.x[:1], w.y[:1], w.z[:1], w.qx, w.qy, 1)
+    assert zq[0] == pytest.approx(float(w.z[0]), rel=1e-7)
+
+
+def test_non_default_stream_and_two_live_grids(aidw, oracle):
+    import torch
+    s = torch.cuda.Stream()
+    a = inputs.uniform_kilo(n=7000, m=2000, seed=56)
+    b = inputs.clustered_kilo(n=9000, m=2000, seed=57)
+    pa, pb = aidw.Params(k=10), aidw.Params(k=16)
+    with torch.cuda.stream(s):
+        ga = aidw.aidw_grid_build(dev(a.x), dev(a.y), dev(a.z), pa, stream=s)
+        gb = aidw.aidw_grid_build(dev(b.x), dev(b.y), dev(b.z), pb, stream=s)
+        za, _ = aidw.aidw_interpolate(ga, dev(a.qx), dev(a.qy), pa, stream=s)
+        zb, _ = aidw.aidw_interpolate(gb, dev(b.qx), dev(b.qy), pb, stream=s)
+        za2, _ = aidw.aidw_interpolate(ga, dev(a.qx), dev(a.qy), pa, stream=s)
+    s.synchronize()
+    ra = oracle.aidw(a.x, a.y, a.z, a.qx, a.qy, 10)
+    rb = oracle.aidw(b.x, b.y, b.z, b.qx, b.qy, 16)
+    assert oracle.normalized_error(host(za), ra["z"], ra["scale"]).max() <= TOL_FP32
+    assert oracle.normalized_error(host(zb), rb["z"], rb["scale"]).max() <= TOL_FP32
+    np.testing.assert_array_equal(host(za2), host(za))    # deterministic
+    ga.destroy()
+    gb.destroy()
+
+
+def test_repeated_calls_are_bitwise_deterministic(aidw):
+    w = inputs.clustered_kilo(n=20000, m=5000, seed=58)
+    outs = [_run(aidw, w.x, w.y, w.z, w.qx, w.qy, 10)[0] for _ in range(3)]
+    np.testing.assert_array_equal(outs[0], outs[1])
+    np.testing.assert_array_equal(outs[0], outs[2])
