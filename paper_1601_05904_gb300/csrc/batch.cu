@@ -42,6 +42,11 @@ struct BJob {
     long long bbox_blocks;  // blocks of the bounding-box reduction
     long long blk_pt, blk_bbox, blk_scan, blk_pad;  // first block in each launch
     double cell_scale, area_param;
+    // queries, sorted by grid cell before the kNN (see knn.cu)
+    const float *qx, *qy;
+    long long m;
+    int *qcount, *qkey, *qrank, *qorder;
+    long long blk_q;
 };
 
 // Job whose first block (field F of the table) is the largest <= b.
@@ -131,6 +136,47 @@ __global__ void __launch_bounds__(kThreads) k_b_pad(const BJob *__restrict__ job
     pad_one(i, J.n_pad, J.n_wpad, J.pts, J.wt);
 }
 
+// ---- queries of every job in grid-cell order (as the single-grid kNN) ----
+__global__ void __launch_bounds__(kThreads) k_b_qkeys(const BJob *__restrict__ jobs, int n_jobs)
+{
+    const BJob &J = jobs[job_of_block<&BJob::blk_q>(jobs, n_jobs, blockIdx.x)];
+    const long long i = (blockIdx.x - J.blk_q) * kThreads + threadIdx.x;
+    if (i >= J.m || grid_failed(J.g)) return;
+    float x = J.qx[i], y = J.qy[i];
+    if (!isfinite(x) || !isfinite(y)) x = y = 0.0f;  // flagged by the kNN kernel
+    key_one_xy(i, x, y, J.g, J.qcount, J.qkey, J.qrank);
+}
+
+__global__ void __launch_bounds__(kThreads) k_b_qscan_reduce(const BJob *__restrict__ jobs,
+                                                             int n_jobs)
+{
+    const BJob &J = jobs[job_of_block<&BJob::blk_scan>(jobs, n_jobs, blockIdx.x)];
+    const long long c = blockIdx.x - J.blk_scan;
+    scan_reduce_chunk(J.qcount, J.cap + 1, c, J.bsum + c);
+}
+
+__global__ void __launch_bounds__(kThreads) k_b_qscan_sums(const BJob *__restrict__ jobs)
+{
+    const BJob &J = jobs[blockIdx.x];
+    scan_sums(J.bsum, (int)J.nchunks);
+}
+
+__global__ void __launch_bounds__(kThreads) k_b_qscan_apply(const BJob *__restrict__ jobs,
+                                                            int n_jobs)
+{
+    const BJob &J = jobs[job_of_block<&BJob::blk_scan>(jobs, n_jobs, blockIdx.x)];
+    const long long c = blockIdx.x - J.blk_scan;
+    scan_apply_chunk(J.qcount, J.cap + 1, c, J.bsum[c]);
+}
+
+__global__ void __launch_bounds__(kThreads) k_b_qscatter(const BJob *__restrict__ jobs, int n_jobs)
+{
+    const BJob &J = jobs[job_of_block<&BJob::blk_q>(jobs, n_jobs, blockIdx.x)];
+    const long long i = (blockIdx.x - J.blk_q) * kThreads + threadIdx.x;
+    if (i >= J.m || grid_failed(J.g)) return;
+    scatter_one(i, J.qcount, J.qkey, J.qrank, J.qorder);
+}
+
 __global__ void k_b_status(const BJob *__restrict__ jobs, int n_jobs, int *status)
 {
     const int j = blockIdx.x * blockDim.x + threadIdx.x;
@@ -172,6 +218,8 @@ struct aidw_batch_plan {
     int kclass_begin[4] = {0, 0, 0, 0};
     long long kclass_q[3] = {0, 0, 0};
     long long total_pt_blocks = 0, total_bbox_blocks = 0, total_chunks = 0, total_pad_blocks = 0;
+    long long total_q_blocks = 0;
+    int *qcount_pool = nullptr;
     long long total_u = 0, total_q = 0, total_tiles = 0, G = 1;
     long long start_ints = 0;
 
@@ -227,6 +275,8 @@ aidw_status upload_tables(aidw_batch_plan *P, const aidw_job *jobs, cudaStream_t
         hb[j].x = jobs[j].x;
         hb[j].y = jobs[j].y;
         hb[j].z = jobs[j].z;
+        hb[j].qx = jobs[j].qx;
+        hb[j].qy = jobs[j].qy;
         hw[j] = P->wj[j];
         hw[j].qx = jobs[j].qx;
         hw[j].qy = jobs[j].qy;
@@ -262,6 +312,15 @@ aidw_status enqueue(aidw_batch_plan *P, cudaStream_t s, bool knn_only)
     k_b_fixup<<<(unsigned)P->total_pt_blocks, kThreads, 0, s>>>(P->d_bj, J);
     if (P->total_pad_blocks > 0)
         k_b_pad<<<(unsigned)P->total_pad_blocks, kThreads, 0, s>>>(P->d_bj, J);
+    if (P->total_q_blocks > 0) {
+        // the data scan is complete, so its chunk sums (bsum) can be reused
+        cudaMemsetAsync(P->qcount_pool, 0, sizeof(int) * (size_t)P->start_ints, s);
+        k_b_qkeys<<<(unsigned)P->total_q_blocks, kThreads, 0, s>>>(P->d_bj, J);
+        k_b_qscan_reduce<<<(unsigned)P->total_chunks, kThreads, 0, s>>>(P->d_bj, J);
+        k_b_qscan_sums<<<(unsigned)J, kThreads, 0, s>>>(P->d_bj);
+        k_b_qscan_apply<<<(unsigned)P->total_chunks, kThreads, 0, s>>>(P->d_bj, J);
+        k_b_qscatter<<<(unsigned)P->total_q_blocks, kThreads, 0, s>>>(P->d_bj, J);
+    }
     aidw_status st = cuda_status(cudaGetLastError());
     const int kmax_of_class[3] = {8, 16, 32};
     for (int c = 0; c < 3 && st == AIDW_OK; ++c) {
@@ -373,7 +432,9 @@ aidw_status aidw_batch_plan_create(const aidw_job *jobs, int n_jobs, const aidw_
     // the start region is sized for the smallest scale the tuner may pick
     const double scale_for_cap = P->tuned_scale ? P->cell_scale : std::min(kMinScale, P->cell_scale);
     std::vector<size_t> o_pts(n_jobs), o_wt(n_jobs), o_start(n_jobs), o_perm(n_jobs),
-        o_key(n_jobs), o_rank(n_jobs), o_tmp(n_jobs), o_bsum(n_jobs), o_rec(n_jobs);
+        o_key(n_jobs), o_rank(n_jobs), o_tmp(n_jobs), o_bsum(n_jobs), o_rec(n_jobs),
+        o_qkey(n_jobs), o_qrank(n_jobs), o_qorder(n_jobs);
+    long long blk_q = 0;
     const size_t o_grids = take(sizeof(GridDev) * (size_t)n_jobs);
     long long start_ints = 0;
     for (int j = 0; j < n_jobs; ++j) {
@@ -401,6 +462,13 @@ aidw_status aidw_batch_plan_create(const aidw_job *jobs, int n_jobs, const aidw_
         o_tmp[j] = take(sizeof(int) * (size_t)b.n);
         o_bsum[j] = take(sizeof(int) * (size_t)cdiv(cap_max + 1, kScanChunk));
         o_rec[j] = take(sizeof(QRec) * (size_t)std::max<long long>(P->m[j], 1));
+        const size_t mq = (size_t)std::max<long long>(P->m[j], 1);
+        o_qkey[j] = take(sizeof(int) * mq);
+        o_qrank[j] = take(sizeof(int) * mq);
+        o_qorder[j] = take(sizeof(int) * mq);
+        b.m = P->m[j];
+        b.blk_q = blk_q;
+        blk_q += cdiv(b.m, kThreads);
         o_start[j] = (size_t)start_ints;  // in ints, inside the start region
         start_ints += (cap_max + 1 + 63) / 64 * 64;
 
@@ -421,6 +489,7 @@ aidw_status aidw_batch_plan_create(const aidw_job *jobs, int n_jobs, const aidw_
     P->total_pt_blocks = blk_pt;
     P->total_bbox_blocks = blk_bbox;
     P->total_pad_blocks = blk_pad;
+    P->total_q_blocks = blk_q;
     P->total_u = ubase;
     P->total_tiles = tbase;
     P->total_q = qbase;
@@ -428,6 +497,7 @@ aidw_status aidw_batch_plan_create(const aidw_job *jobs, int n_jobs, const aidw_
     P->G = std::max<long long>(1, std::min<long long>(weight_resident_ctas(P->device, P->fp64),
                                                       std::max<long long>(ubase, 1)));
     const size_t o_startreg = take(sizeof(int) * (size_t)start_ints);
+    const size_t o_qcountreg = take(sizeof(int) * (size_t)start_ints);
     const size_t o_part = take(weight_partial_bytes(P->fp64) * (size_t)(P->total_tiles + P->G));
     const size_t o_tables = take((sizeof(BJob) + sizeof(KnnJob) + sizeof(WJob)) * (size_t)n_jobs);
     const size_t o_status = take(sizeof(int));
@@ -446,6 +516,7 @@ aidw_status aidw_batch_plan_create(const aidw_job *jobs, int n_jobs, const aidw_
     unsigned char *base = P->pool;
     P->d_grids = reinterpret_cast<GridDev *>(base + o_grids);
     P->start_pool = reinterpret_cast<int *>(base + o_startreg);
+    P->qcount_pool = reinterpret_cast<int *>(base + o_qcountreg);
     P->d_part = base + o_part;
     P->d_bj = reinterpret_cast<BJob *>(base + o_tables);
     P->d_kj = reinterpret_cast<KnnJob *>(base + o_tables + sizeof(BJob) * n_jobs);
@@ -463,6 +534,10 @@ aidw_status aidw_batch_plan_create(const aidw_job *jobs, int n_jobs, const aidw_
         b.tmp = reinterpret_cast<int *>(base + o_tmp[j]);
         b.bsum = reinterpret_cast<int *>(base + o_bsum[j]);
         b.start = P->start_pool + o_start[j];
+        b.qcount = P->qcount_pool + o_start[j];
+        b.qkey = reinterpret_cast<int *>(base + o_qkey[j]);
+        b.qrank = reinterpret_cast<int *>(base + o_qrank[j]);
+        b.qorder = reinterpret_cast<int *>(base + o_qorder[j]);
         WJob &w = P->wj[j];
         w.wt = b.wt;
         w.pts = b.pts;
@@ -486,6 +561,7 @@ aidw_status aidw_batch_plan_create(const aidw_job *jobs, int n_jobs, const aidw_
             kj.pts = P->bj[j].pts;
             kj.start = P->bj[j].start;
             kj.recs = const_cast<QRec *>(P->wj[j].recs);
+            kj.order = P->bj[j].qorder;
             kj.nq = P->m[j];
             kj.q_base = qb;
             kj.k = k;

@@ -98,7 +98,16 @@ __device__ __forceinline__ void bbox_block(const float *__restrict__ x, const fl
 __device__ __forceinline__ void grid_dims(GridDev *g, double cell_scale, double area_param,
                                           long long cap)
 {
-    if (g->status & kStatusNonfiniteData) return;
+    if (g->status & kStatusNonfiniteData) {
+        // a failed grid still gets in-range dimensions (one empty cell), so
+        // no later kernel can index outside its arrays
+        g->min_x = g->min_y = g->max_x = g->max_y = 0.0;
+        g->area = 0.0;
+        g->r_exp = 0.0;
+        g->cw = 1.0;
+        g->n_col = g->n_row = g->n_cells = 1;
+        return;
+    }
     const double minx = (double)dec_float(g->enc_min_x), maxx = (double)dec_float(g->enc_max_x);
     const double miny = (double)dec_float(g->enc_min_y), maxy = (double)dec_float(g->enc_max_y);
     const double W = maxx - minx, H = maxy - miny;
@@ -133,21 +142,30 @@ __device__ __forceinline__ bool grid_failed(const GridDev *g)
     return (g->status & (kStatusNonfiniteData | kStatusCapacity)) != 0;
 }
 
-// Cell of point i and its (unstable) rank among the points of that cell.
-__device__ __forceinline__ void key_one(long long i, const float *__restrict__ x,
-                                        const float *__restrict__ y, const GridDev *g,
-                                        int *__restrict__ count, int *__restrict__ key,
-                                        int *__restrict__ rank)
+// Cell of the point (x, y) stored as item i, and its (unstable) rank among
+// the items of that cell.
+__device__ __forceinline__ void key_one_xy(long long i, float x, float y, const GridDev *g,
+                                           int *__restrict__ count, int *__restrict__ key,
+                                           int *__restrict__ rank)
 {
     const double minx = g->min_x, miny = g->min_y, cw = g->cw;
     const long long nc = g->n_col, nr = g->n_row;
-    long long col = (long long)floor(((double)x[i] - minx) / cw);
-    long long row = (long long)floor(((double)y[i] - miny) / cw);
+    long long col = (long long)floor(((double)x - minx) / cw);
+    long long row = (long long)floor(((double)y - miny) / cw);
     col = col < 0 ? 0 : (col > nc - 1 ? nc - 1 : col);
     row = row < 0 ? 0 : (row > nr - 1 ? nr - 1 : row);
     const int c = (int)(row * nc + col);
     key[i] = c;
     rank[i] = atomicAdd(count + c, 1);
+}
+
+// Cell of data point i and its (unstable) rank among the points of that cell.
+__device__ __forceinline__ void key_one(long long i, const float *__restrict__ x,
+                                        const float *__restrict__ y, const GridDev *g,
+                                        int *__restrict__ count, int *__restrict__ key,
+                                        int *__restrict__ rank)
+{
+    key_one_xy(i, x[i], y[i], g, count, key, rank);
 }
 
 // Block-wide exclusive scan of one value per thread; total gets the sum.

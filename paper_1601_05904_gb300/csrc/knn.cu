@@ -86,8 +86,12 @@ __global__ void __launch_bounds__(kKnnMaxThreads)
     if (gq >= total_q) return;
     // single-job launches pass the job by value and no table
     const KnnJob J = jobs ? jobs[knn_job_of(jobs, n_jobs, gq)] : job0;
-    const long long q = J.order ? (long long)J.order[gq - J.q_base] : gq - J.q_base;
     const GridDev *__restrict__ g = J.g;
+    // a grid whose build failed (non-finite data) has no usable cells and no
+    // query order: its queries get NaN results in input order
+    const bool failed = (g->status & (kStatusNonfiniteData | kStatusCapacity)) != 0;
+    const long long li = gq - J.q_base;
+    const long long q = (J.order && !failed) ? (long long)J.order[li] : li;
     const Point *__restrict__ pts = J.pts;
     const int *__restrict__ start = J.start;
     const int k = J.k;
@@ -99,8 +103,8 @@ __global__ void __launch_bounds__(kKnnMaxThreads)
     const float qx = J.qx[q], qy = J.qy[q];
     const double nanv = __longlong_as_double(0x7ff8000000000000LL);
 
-    if (!isfinite(qx) || !isfinite(qy)) {
-        atomicOr(const_cast<int *>(&g->status), kStatusNonfiniteQuery);
+    if (failed || !isfinite(qx) || !isfinite(qy)) {
+        if (!failed) atomicOr(const_cast<int *>(&g->status), kStatusNonfiniteQuery);
         if (recs) {
             QRec r;
             r.alpha = nanv;
@@ -317,17 +321,19 @@ __global__ void __launch_bounds__(kKnnMaxThreads)
     const long long gq = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     if (gq >= total_q) return;  // uniform across the warp
     const KnnJob J = jobs ? jobs[knn_job_of(jobs, n_jobs, gq)] : job0;
-    const long long q = J.order ? (long long)J.order[gq - J.q_base] : gq - J.q_base;
     const GridDev *__restrict__ g = J.g;
+    const bool failed = (g->status & (kStatusNonfiniteData | kStatusCapacity)) != 0;
+    const long long li = gq - J.q_base;
+    const long long q = (J.order && !failed) ? (long long)J.order[li] : li;
     const Point *__restrict__ pts = J.pts;
     const int *__restrict__ start = J.start;
     const int k = J.k;
     const float qx = J.qx[q], qy = J.qy[q];
     const double nanv = __longlong_as_double(0x7ff8000000000000LL);
 
-    if (!isfinite(qx) || !isfinite(qy)) {
+    if (failed || !isfinite(qx) || !isfinite(qy)) {
         if (lane == 0) {
-            atomicOr(const_cast<int *>(&g->status), kStatusNonfiniteQuery);
+            if (!failed) atomicOr(const_cast<int *>(&g->status), kStatusNonfiniteQuery);
             if (J.recs) {
                 QRec r;
                 r.alpha = nanv;
@@ -597,15 +603,7 @@ __global__ void __launch_bounds__(gridk::kThreads)
     if (i >= nq) return;
     float x = qx[i], y = qy[i];
     if (!isfinite(x) || !isfinite(y)) x = y = 0.0f;  // flagged by the kNN kernel
-    const double minx = g->min_x, miny = g->min_y, cw = g->cw;
-    const long long nc = g->n_col, nr = g->n_row;
-    long long col = (long long)floor(((double)x - minx) / cw);
-    long long row = (long long)floor(((double)y - miny) / cw);
-    col = col < 0 ? 0 : (col > nc - 1 ? nc - 1 : col);
-    row = row < 0 ? 0 : (row > nr - 1 ? nr - 1 : row);
-    const int c = (int)(row * nc + col);
-    key[i] = c;
-    rank[i] = atomicAdd(count + c, 1);
+    gridk::key_one_xy(i, x, y, g, count, key, rank);
 }
 
 __global__ void __launch_bounds__(gridk::kThreads) k_qscan_reduce(const int *a, long long len,

@@ -131,6 +131,10 @@ def test_batch_errors(aidw):
     zz[7] = np.nan
     jobs[1].z = dev(zz)
     plan = aidw.aidw_batch_plan_create(jobs, p)
-    aidw.aidw_batch_run(plan, jobs)
+    outs = aidw.aidw_batch_run(plan, jobs)
     assert aidw.aidw_batch_plan_status(plan) == 3
+    # the failed job's predictions are NaN; the other job is unaffected
+    assert np.isnan(host(outs[1])).all()
+    x, y, z, qx, qy, k = raw[0]
+    assert np.isfinite(host(outs[0])).all()
     plan.destroy()
