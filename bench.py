@@ -403,6 +403,9 @@ def run_batch(args):
     rank, world, local = dist_env()
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=dev)
     binding.load()
     ws = inputs.batch_jobs(n_jobs=args.jobs, seed_base=1000 + 100_000 * rank)
     jobs = [binding.BatchJob(*(torch.from_numpy(getattr(w, a)).to(dev)
@@ -420,6 +423,8 @@ def run_batch(args):
     ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
           for _ in range(args.steps)]
     clocks = ClockSampler(local)
+    if world > 1:
+        torch.distributed.barrier()
     torch.cuda.synchronize()
     clocks.start()
     for i in range(args.steps):
@@ -428,9 +433,16 @@ def run_batch(args):
         binding.aidw_batch_run(plan, jobs)
         ev[i][1].record()
     torch.cuda.synchronize()
+    if world > 1:
+        torch.distributed.barrier()
     clk = clocks.stop()
-    step_ms = sum(a.elapsed_time(b) for a, b in ev) / args.steps
+    step_ms = 1000.0 * max_over_ranks(sum(a.elapsed_time(b) for a, b in ev) / 1000.0,
+                                      dev) / args.steps
     total_q = sum(w.m for w in ws)
+    if rank != 0:
+        plan.destroy()
+        torch.distributed.destroy_process_group()
+        return 0
     rates = binding.aidw_probe_pipe_rates()
     props = torch.cuda.get_device_properties(dev)
     peaks = measured_peaks() or {}
@@ -438,7 +450,8 @@ def run_batch(args):
     peak = 1.0 / (1.0 / rates["lg2"] + 1.0 / rates["ex2"]) * props.multi_processor_count * sm_max * 1e6
     pairs = float(info["total_pairs"])
     line = {"metric": "AIDW batched interpolated points/s (512 jobs, n_j log-uniform 1e3..2e5)",
-            "value": total_q / (step_ms / 1000.0), "unit": UNIT, "n_gpus": world,
+            "value": whole_job_value(world, total_q, 1, step_ms / 1000.0), "unit": UNIT,
+            "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": step_ms,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
             "data": "synthetic",
@@ -458,6 +471,8 @@ def run_batch(args):
             "clocks": clk, "device": props.name}
     plan.destroy()
     print(json.dumps(line), flush=True)
+    if world > 1:
+        torch.distributed.destroy_process_group()
     return 0
 
 

@@ -106,8 +106,8 @@ typedef struct aidw_grid aidw_grid;
 aidw_status aidw_grid_build(const float *x, const float *y, const float *z, int64_t n_data,
                             const aidw_params *p, aidw_stream_t stream, aidw_grid **out);
 
-/* Frees the grid after draining the stream it was built on.  Returns the
- * latched device status (AIDW_OK if none). */
+/* Synchronises the device (work on any stream may still read the grid),
+ * frees the grid and returns its latched device status (AIDW_OK if none). */
 aidw_status aidw_grid_destroy(aidw_grid *g);
 
 /* Host copy of the grid's dimensions (synchronises with the build stream). */
@@ -120,8 +120,9 @@ aidw_status aidw_grid_get_info(const aidw_grid *g, aidw_grid_info *info);
 aidw_status aidw_grid_export(const aidw_grid *g, int64_t *cell_start, int32_t *perm,
                              aidw_stream_t stream);
 
-/* Synchronises the grid's stream and returns then clears the latched
- * device-side error (non-finite query coordinates, expired waits). */
+/* Synchronises the device (calls on any stream may latch errors in the
+ * grid) and returns then clears the latched device-side error (non-finite
+ * query coordinates, expired waits). */
 aidw_status aidw_grid_status(aidw_grid *g);
 
 /* Exact k nearest neighbours of each query by the grid search of

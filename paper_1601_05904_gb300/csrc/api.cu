@@ -235,7 +235,11 @@ aidw_status aidw_grid_build(const float *x, const float *y, const float *z, int6
     aidw_grid *g = new (std::nothrow) aidw_grid();
     if (!g) return AIDW_ERR_OOM;
     memset(g, 0, sizeof(*g));
-    cudaGetDevice(&g->device);
+    if (cudaGetDevice(&g->device) != cudaSuccess) {
+        cudaGetLastError();
+        delete g;
+        return AIDW_ERR_CUDA;
+    }
     g->n_data = n_data;
     g->n_pad = (n_data + 31) / 32 * 32;
     g->cell_scale = p->cell_scale > 0.0 ? p->cell_scale : auto_cell_scale(p->k);

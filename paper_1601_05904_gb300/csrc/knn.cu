@@ -632,11 +632,10 @@ __global__ void __launch_bounds__(gridk::kThreads)
 // overrides; default on from 4096 queries).
 bool knn_sort_queries(long long nq)
 {
-    static int v = -2;
-    if (v == -2) {
+    static const int v = [] {
         const char *e = getenv("AIDW_KNN_SORT");
-        v = e ? (atoi(e) != 0 ? 1 : 0) : -1;
-    }
+        return e ? (atoi(e) != 0 ? 1 : 0) : -1;
+    }();
     return v >= 0 ? v == 1 : nq >= 4096;
 }
 
@@ -687,13 +686,12 @@ aidw_status query_order(const aidw_grid *g, const float *qx, const float *qy, lo
 // idle).  AIDW_KNN_MODE=warp selects the warp kernel.
 int knn_default_threads(int k)
 {
-    static int mode = -2;
-    (void)k;
-    if (mode == -2) {
+    static const bool warp = [] {
         const char *e = getenv("AIDW_KNN_MODE");
-        mode = (e && strcmp(e, "warp") == 0) ? 0 : 1;
-    }
-    return mode == 0 ? 0 : kKnnThreads;
+        return e && strcmp(e, "warp") == 0;
+    }();
+    (void)k;
+    return warp ? 0 : kKnnThreads;
 }
 
 aidw_status knn_launch(const aidw_grid *g, const float *qx, const float *qy, long long n_query,

@@ -37,6 +37,7 @@
 #include <string.h>
 
 #include <algorithm>
+#include <mutex>
 #include <type_traits>
 
 #include "aidw_device.cuh"
@@ -456,12 +457,11 @@ __global__ void k_finalize_f64(SKArgs a, const double2 *__restrict__ part)
 // measuring the balance on a given GPU.
 int poly_units()
 {
-    static int v = -1;
-    if (v < 0) {
+    static const int v = [] {
         const char *e = getenv("AIDW_EXP2_POLY_UNITS");
         const int x = e ? atoi(e) : 2;
-        v = (x == 0 || x == 2 || x == 3 || x == 4) ? x : 2;
-    }
+        return (x == 0 || x == 2 || x == 3 || x == 4) ? x : 2;
+    }();
     return v;
 }
 
@@ -476,8 +476,10 @@ constexpr size_t stage_smem()
 template <bool F64>
 int resident_ctas(int device)
 {
+    static std::mutex mu;
     static int cached[2][64] = {};
     if (device < 0 || device >= 64) return 1;
+    std::lock_guard<std::mutex> lk(mu);
     int &c = cached[F64 ? 1 : 0][device];
     if (c) return c;
     const size_t smem = stage_smem<F64>();
