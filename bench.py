@@ -52,7 +52,8 @@ def parse():
     ap.add_argument("--no-tune", action="store_true", help="batch: skip the autotuner")
     ap.add_argument("--cell-scale", type=float, default=0.0,
                     help="grid cell width / r_exp (<= 0: the library's choice)")
-    ap.add_argument("--mode", choices=("aidw", "local", "knn-table", "sweep"), default="aidw",
+    ap.add_argument("--mode", choices=("aidw", "local", "knn", "knn-table", "sweep"),
+                    default="aidw",
                     help="aidw: Eq. 1 over all points; local: Eq. 1 over the k nearest; "
                          "knn-table: grid vs all-points kNN at the paper's sizes; "
                          "sweep: the full step at the paper's sizes")
@@ -257,10 +258,14 @@ def run_ours(args):
 
     interp = (binding.aidw_interpolate_local if args.mode == "local"
               else binding.aidw_interpolate)
+    robs = torch.empty(w.m, dtype=torch.float32, device=dev)
 
     def step():
         g = binding.aidw_grid_build(t["x"], t["y"], t["z"], params)
-        interp(g, t["qx"], t["qy"], params, out_z=out_z)
+        if args.mode == "knn":
+            binding.aidw_knn(g, t["qx"], t["qy"], w.k, out_robs=robs, want=("robs",))
+        else:
+            interp(g, t["qx"], t["qy"], params, out_z=out_z)
         g.destroy()
 
     for _ in range(args.warmup):
@@ -296,7 +301,7 @@ def run_ours(args):
 
     # float64 plain path on a query sample (kNN + weighting + grid build)
     fp64 = None
-    if args.fp64_queries > 0 and rank == 0:
+    if args.fp64_queries > 0 and rank == 0 and args.mode != "knn":
         mq = min(args.fp64_queries, w.m)
         p64 = pkg.Params(k=w.k, precision=binding.AIDW_FP64_PLAIN)
         qx64, qy64 = t["qx"][:mq].contiguous(), t["qy"][:mq].contiguous()
@@ -359,7 +364,7 @@ def run_ours(args):
                                f"{pairs_per_sm_clk:.2f} pairs per SM per clock x "
                                f"{props.multi_processor_count} SMs x {sm_max:.0f} MHz max clock"),
                 "pipe_rates_per_sm_clk": rates}
-    if args.mode == "local":
+    if args.mode in ("local", "knn"):
         # kNN + local weighting in one kernel: algorithmic bytes are the
         # queries (8 B in, 4 B out) and the data set read once (16 B points
         # + 4 B z + 4 B cell head per point)
@@ -367,7 +372,8 @@ def run_ours(args):
         alg = 12.0 * w.m + 24.0 * w.n
         hbm = float(peaks.get("hbm_gbs", 6800.0))
         ach = alg / (k_ms / k_launches / 1000.0) / 1e9 if k_launches else None
-        roofline = {"bound": "hbm", "kernel": "k_knn (grid kNN + local weighting)",
+        roofline = {"bound": "hbm", "kernel": "k_knn (grid kNN" +
+                    (" + local weighting)" if args.mode == "local" else ")"),
                     "achieved": ach, "peak": hbm, "unit": "GB/s",
                     "frac": (ach / hbm) if ach else None, "traffic": None,
                     "peak_basis": "MEASURED_PEAKS.json hbm_gbs (copy); the kernel is bound by "
@@ -376,8 +382,9 @@ def run_ours(args):
     cpu = None
     if not args.no_cpu_baseline and world >= 1:
         cpu = cpu_baseline(w, args.cpu_seconds, rank)
-    metric = METRIC if args.mode == "aidw" else \
-        "local AIDW interpolated points/s at n=m=1M (kNN + Eq. 1 over the k nearest)"
+    metric = {"aidw": METRIC,
+              "local": "local AIDW interpolated points/s at n=m=1M (kNN + Eq. 1 over the k nearest)",
+              "knn": "grid build + kNN queries/s at n=m=1M (r_obs per query)"}[args.mode]
     line = {"metric": metric, "value": value, "unit": UNIT, "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": step_ms,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
