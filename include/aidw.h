@@ -265,6 +265,14 @@ aidw_status aidw_interpolate_local(const aidw_grid *g, const float *qx, const fl
                                    int64_t n_query, const aidw_params *p, void *out_z,
                                    void *out_alpha, aidw_stream_t stream);
 
+/* Caps the device memory the library holds at once from its pool (grids and
+ * per-call scratch, not batch plans): a call that would pass the cap fails
+ * with AIDW_ERR_OOM before any work.  bytes = 0 removes the cap.  *held (may
+ * be NULL) receives the bytes held now.  A library service with no
+ * counterpart in the paper (memory budgets, and testing the OOM path without
+ * exhausting the GPU). */
+aidw_status aidw_set_memory_limit(int64_t bytes, int64_t *held);
+
 /* Short English name of a status code (static storage). */
 const char *aidw_status_string(aidw_status s);
 

@@ -122,6 +122,8 @@ def load(path: str | None = None):
         lib.aidw_knn_bruteforce.argtypes = [vp, vp, vp, i64, c_int, vp, vp, vp, vp]
         lib.aidw_interpolate_local.restype = c_int
         lib.aidw_interpolate_local.argtypes = [vp, vp, vp, i64, P(CParams), vp, vp, vp]
+        lib.aidw_set_memory_limit.restype = c_int
+        lib.aidw_set_memory_limit.argtypes = [i64, P(i64)]
         lib.aidw_profile_enable.restype = c_int
         lib.aidw_profile_enable.argtypes = [c_int]
         lib.aidw_profile_read.restype = c_int
@@ -322,6 +324,14 @@ def aidw_interpolate_local(grid: Grid, qx, qy, params: Params | None = None, out
                                          _ptr(out_z), _ptr(out_alpha), _stream(stream)),
            "aidw_interpolate_local")
     return out_z, out_alpha
+
+
+def aidw_set_memory_limit(nbytes: int) -> int:
+    """Caps the library's pool memory (0: no cap); returns the bytes held now."""
+    held = ctypes.c_int64()
+    _check(load().aidw_set_memory_limit(int(nbytes), ctypes.byref(held)),
+           "aidw_set_memory_limit")
+    return held.value
 
 
 def aidw_profile_enable(on: bool = True) -> None:

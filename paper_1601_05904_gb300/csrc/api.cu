@@ -6,6 +6,7 @@
 
 #include <mutex>
 #include <new>
+#include <unordered_map>
 #include <vector>
 
 #include "aidw_internal.cuh"
@@ -51,25 +52,54 @@ cudaMemPool_t pool_for(int device)
 }
 }  // namespace api_detail
 
+// Optional cap on the bytes the library holds from its pool at once (0: no
+// cap); allocations past it fail with cudaErrorMemoryAllocation (reported as
+// AIDW_ERR_OOM) without touching the device.
+namespace api_detail {
+std::mutex g_cap_mu;
+size_t g_cap_bytes = 0;
+size_t g_held_bytes = 0;
+std::unordered_map<void *, size_t> g_sizes;
+}  // namespace api_detail
+
 cudaError_t lib_alloc(void **p, size_t bytes, cudaStream_t s)
 {
+    using namespace api_detail;
     *p = nullptr;
+    if (bytes == 0) bytes = 1;
+    {
+        std::lock_guard<std::mutex> lk(g_cap_mu);
+        if (g_cap_bytes && g_held_bytes + bytes > g_cap_bytes) return cudaErrorMemoryAllocation;
+    }
     int device = 0;
     cudaError_t e = cudaGetDevice(&device);
     if (e != cudaSuccess) return e;
-    cudaMemPool_t pool = api_detail::pool_for(device);
-    e = pool ? cudaMallocFromPoolAsync(p, bytes > 0 ? bytes : 1, pool, s)
-             : cudaMallocAsync(p, bytes > 0 ? bytes : 1, s);
+    cudaMemPool_t pool = pool_for(device);
+    e = pool ? cudaMallocFromPoolAsync(p, bytes, pool, s) : cudaMallocAsync(p, bytes, s);
     if (e != cudaSuccess) {
         cudaGetLastError();
         *p = nullptr;
+        return e;
     }
+    std::lock_guard<std::mutex> lk(g_cap_mu);
+    g_sizes[*p] = bytes;
+    g_held_bytes += bytes;
     return e;
 }
 
 void lib_free(void *p, cudaStream_t s)
 {
-    if (p) cudaFreeAsync(p, s);
+    using namespace api_detail;
+    if (!p) return;
+    {
+        std::lock_guard<std::mutex> lk(g_cap_mu);
+        auto it = g_sizes.find(p);
+        if (it != g_sizes.end()) {
+            g_held_bytes -= it->second;
+            g_sizes.erase(it);
+        }
+    }
+    cudaFreeAsync(p, s);
 }
 
 // ---- stage timing ------------------------------------------------------------
@@ -416,6 +446,15 @@ aidw_status aidw_interpolate_local(const aidw_grid *g, const float *qx, const fl
     return knn_launch(g, qx, qy, n_query, p->k, p->precision == AIDW_FP64_PLAIN,
                       alpha_params(p), nullptr, nullptr, nullptr, nullptr, out_alpha,
                       reinterpret_cast<cudaStream_t>(stream), out_z);
+}
+
+aidw_status aidw_set_memory_limit(int64_t bytes, int64_t *held)
+{
+    if (bytes < 0) return AIDW_ERR_INVALID_ARG;
+    std::lock_guard<std::mutex> lk(g_cap_mu);
+    g_cap_bytes = (size_t)bytes;
+    if (held) *held = (int64_t)g_held_bytes;
+    return AIDW_OK;
 }
 
 aidw_status aidw_profile_enable(int on)

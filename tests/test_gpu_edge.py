@@ -115,3 +115,53 @@ def test_repeated_calls_are_bitwise_deterministic(aidw):
     outs = [_run(aidw, w.x, w.y, w.z, w.qx, w.qy, 10)[0] for _ in range(3)]
     np.testing.assert_array_equal(outs[0], outs[1])
     np.testing.assert_array_equal(outs[0], outs[2])
+
+
+def test_memory_cap_reports_oom_and_recovers(aidw):
+    """The OOM path, forced through the library's pool cap (no real
+    exhaustion of the GPU)."""
+    w = inputs.uniform_kilo(n=200000, m=5000, seed=59)
+    p = aidw.Params()
+    assert aidw.aidw_set_memory_limit(1 << 20) >= 0
+    try:
+        with pytest.raises(aidw.AidwError) as e:
+            aidw.aidw_grid_build(dev(w.x), dev(w.y), dev(w.z), p)
+        assert e.value.status == 4
+    finally:
+        aidw.aidw_set_memory_limit(0)
+    g = aidw.aidw_grid_build(dev(w.x), dev(w.y), dev(w.z), p)
+    # a cap between the grid and the call's scratch fails the call, not the grid
+    held = aidw.aidw_set_memory_limit(0)
+    aidw.aidw_set_memory_limit(held + 1024)
+    try:
+        with pytest.raises(aidw.AidwError) as e:
+            aidw.aidw_interpolate(g, dev(w.qx), dev(w.qy), p)
+        assert e.value.status == 4
+    finally:
+        aidw.aidw_set_memory_limit(0)
+    z, _ = aidw.aidw_interpolate(g, dev(w.qx), dev(w.qy), p)
+    assert np.isfinite(host(z)).all()
+    assert aidw.aidw_grid_status(g) == 0
+    g.destroy()
+
+
+def test_data_order_permutation(aidw, oracle):
+    """Permuting the data points changes nothing but the indices (ties are
+    broken by index, so compare distances and mapped index sets)."""
+    w = inputs.clustered_kilo(n=20000, m=3000, seed=60)
+    perm = np.random.default_rng(60).permutation(w.n)
+    p = aidw.Params(k=12)
+    g1 = aidw.aidw_grid_build(dev(w.x), dev(w.y), dev(w.z), p)
+    g2 = aidw.aidw_grid_build(dev(w.x[perm]), dev(w.y[perm]), dev(w.z[perm]), p)
+    i1, d1, r1 = (host(t) for t in aidw.aidw_knn(g1, dev(w.qx), dev(w.qy), 12))
+    i2, d2, r2 = (host(t) for t in aidw.aidw_knn(g2, dev(w.qx), dev(w.qy), 12))
+    np.testing.assert_array_equal(d2, d1)
+    np.testing.assert_array_equal(r2, r1)
+    same = np.array([set(a) == set(b) for a, b in zip(i1.tolist(), perm[i2].tolist())])
+    assert same.mean() > 0.999
+    z1, a1 = aidw.aidw_interpolate(g1, dev(w.qx), dev(w.qy), p, want_alpha=True)
+    z2, a2 = aidw.aidw_interpolate(g2, dev(w.qx), dev(w.qy), p, want_alpha=True)
+    np.testing.assert_array_equal(host(a2), host(a1))
+    np.testing.assert_allclose(host(z2), host(z1), rtol=0, atol=2e-6 * np.abs(w.z).max())
+    g1.destroy()
+    g2.destroy()
