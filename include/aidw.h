@@ -110,7 +110,8 @@ aidw_status aidw_grid_build(const float *x, const float *y, const float *z, int6
  * frees the grid and returns its latched device status (AIDW_OK if none). */
 aidw_status aidw_grid_destroy(aidw_grid *g);
 
-/* Host copy of the grid's dimensions (synchronises with the build stream). */
+/* The grid's dimensions (a host copy taken when the build returned; no
+ * device access). */
 aidw_status aidw_grid_get_info(const aidw_grid *g, aidw_grid_info *info);
 
 /* Copies the grid's cell heads and cell-ordered permutation into caller

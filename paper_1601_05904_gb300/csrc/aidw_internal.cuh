@@ -66,7 +66,7 @@ struct aidw_grid {
     long long cap_cells;         // capacity of cell_start minus one
     double cell_scale;
     double area_param;
-    cudaStream_t stream;         // build stream (drained on destroy)
+    aidw::GridDev host_copy;     // the device record as it was when the build returned
     int device;
 };
 

@@ -275,7 +275,6 @@ aidw_status aidw_grid_build(const float *x, const float *y, const float *z, int6
     g->cell_scale = p->cell_scale > 0.0 ? p->cell_scale : auto_cell_scale(p->k);
     g->area_param = p->area > 0.0 ? p->area : 0.0;
     g->cap_cells = grid_cells_capacity(n_data, g->cell_scale);
-    g->stream = s;
 
     cudaError_t e = lib_alloc((void **)&g->dev, sizeof(GridDev), s);
     if (e == cudaSuccess) e = lib_alloc((void **)&g->pts, sizeof(Point) * (size_t)g->n_pad, s);
@@ -296,8 +295,9 @@ aidw_status aidw_grid_build(const float *x, const float *y, const float *z, int6
     aidw_status st = grid_build_launch(g, x, y, z, s);
     if (st == AIDW_OK) st = cuda_status(cudaStreamSynchronize(s));
     if (st == AIDW_OK) {
-        int status = 0;
-        st = cuda_status(cudaMemcpy(&status, &g->dev->status, sizeof(int), cudaMemcpyDeviceToHost));
+        st = cuda_status(cudaMemcpy(&g->host_copy, g->dev, sizeof(GridDev),
+                                    cudaMemcpyDeviceToHost));
+        const int status = g->host_copy.status;
         if (st == AIDW_OK && (status & kStatusNonfiniteData)) st = AIDW_ERR_NONFINITE;
         if (st == AIDW_OK && (status & kStatusCapacity)) st = AIDW_ERR_INVALID_ARG;
     }
@@ -347,10 +347,7 @@ aidw_status aidw_grid_destroy(aidw_grid *g)
 aidw_status aidw_grid_get_info(const aidw_grid *g, aidw_grid_info *info)
 {
     if (!g || !info) return AIDW_ERR_INVALID_ARG;
-    GridDev d;
-    cudaError_t e = cudaStreamSynchronize(g->stream);
-    if (e == cudaSuccess) e = cudaMemcpy(&d, g->dev, sizeof(GridDev), cudaMemcpyDeviceToHost);
-    if (e != cudaSuccess) return cuda_status(e);
+    const GridDev &d = g->host_copy;  // dimensions are fixed once the build returns
     info->n_data = d.n_data;
     info->n_col = d.n_col;
     info->n_row = d.n_row;

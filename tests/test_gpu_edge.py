@@ -165,3 +165,34 @@ def test_data_order_permutation(aidw, oracle):
     np.testing.assert_allclose(host(z2), host(z1), rtol=0, atol=2e-6 * np.abs(w.z).max())
     g1.destroy()
     g2.destroy()
+
+
+def test_interpolate_replays_in_a_cuda_graph(aidw, oracle):
+    """aidw_interpolate enqueues only stream-ordered allocations, memsets and
+    kernels, so it can be captured once and replayed on new query values."""
+    import torch
+    w = inputs.clustered_kilo(n=30000, m=6000, seed=62)
+    p = aidw.Params(k=10)
+    g = aidw.aidw_grid_build(dev(w.x), dev(w.y), dev(w.z), p)
+    qx, qy = dev(w.qx), dev(w.qy)
+    out = torch.empty(w.m, dtype=torch.float32, device="cuda")
+    s = torch.cuda.Stream()
+    with torch.cuda.stream(s):
+        aidw.aidw_interpolate(g, qx, qy, p, out_z=out, stream=s)   # first call outside
+    s.synchronize()
+    graph = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(graph, stream=s):
+        aidw.aidw_interpolate(g, qx, qy, p, out_z=out, stream=s)
+    rng = np.random.default_rng(63)
+    for _ in range(2):
+        nqx, nqy = inputs.uniform_points(rng, w.m, 0.0, 1000.0)
+        qx.copy_(dev(nqx))
+        qy.copy_(dev(nqy))
+        out.fill_(float("nan"))
+        graph.replay()
+        torch.cuda.synchronize()
+        ref = oracle.aidw(w.x, w.y, w.z, nqx, nqy, 10)
+        err = oracle.normalized_error(host(out), ref["z"], ref["scale"])
+        assert err.max() <= TOL_FP32
+    del graph
+    g.destroy()
