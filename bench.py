@@ -178,25 +178,53 @@ def measured_peaks():
     return None
 
 
-def cpu_baseline(w, seconds: float, rank: int):
-    """The oracle as it stands, on the host cores, over a bounded query sample."""
+def cpu_baseline(w, seconds: float, rank: int, local: bool = False):
+    """The oracle as it stands, on the host cores, over a bounded query sample.
+    Returns (baseline dict, sample indices, oracle results on the sample)."""
     import oracle
     from paper_1601_05904_gb300 import inputs
     oracle.build()
+    fn = oracle.aidw_local if local else oracle.aidw
     cores = oracle.num_threads()
     probe = max(cores, 8)
     s = inputs.query_subsample(w.m, probe, seed=2024 + rank)
     t0 = time.perf_counter()
-    oracle.aidw(w.x, w.y, w.z, w.qx[s], w.qy[s], w.k)
+    fn(w.x, w.y, w.z, w.qx[s], w.qy[s], w.k)
     per_q = (time.perf_counter() - t0) / probe
     count = int(max(probe, min(w.m, seconds / max(per_q, 1e-9))))
     s = inputs.query_subsample(w.m, count, seed=4048 + rank)
     t0 = time.perf_counter()
-    oracle.aidw(w.x, w.y, w.z, w.qx[s], w.qy[s], w.k)
+    ref = fn(w.x, w.y, w.z, w.qx[s], w.qy[s], w.k)
     dt = time.perf_counter() - t0
-    return {"value": count / dt, "unit": UNIT, "cores": cores, "kind": "oracle",
-            "sample": f"{count} of {w.m} queries against all {w.n} data points "
-                      f"({dt:.1f} s, FP64, brute-force kNN with full sort)"}
+    return ({"value": count / dt, "unit": UNIT, "cores": cores, "kind": "oracle",
+             "sample": f"{count} of {w.m} queries against all {w.n} data points "
+                       f"({dt:.1f} s, FP64, brute-force kNN with full sort)"}, s, ref)
+
+
+def accuracy_on_sample(binding, pkg, t, w, s, ref, params, local, z32_all):
+    """Error of the GPU predictions against the oracle on the baseline's
+    sample: max |z - z_ref| / S_q (S_q = sum w|z| / sum w) for the FP32-comp
+    output of the timed steps and for the FP64 path run on the same queries,
+    and the largest alpha difference."""
+    import oracle
+    import torch
+    interp = binding.aidw_interpolate_local if local else binding.aidw_interpolate
+    idx = torch.from_numpy(s).to(t["qx"].device)
+    qx, qy = t["qx"][idx].contiguous(), t["qy"][idx].contiguous()
+    g = binding.aidw_grid_build(t["x"], t["y"], t["z"], params)
+    _, a32 = interp(g, qx, qy, params, want_alpha=True)
+    p64 = pkg.Params(k=params.k, precision=binding.AIDW_FP64_PLAIN)
+    z64, _ = interp(g, qx, qy, p64)
+    torch.cuda.synchronize()
+    g.destroy()
+    e32 = oracle.normalized_error(z32_all[s], ref["z"], ref["scale"])
+    e64 = oracle.normalized_error(z64.cpu().numpy(), ref["z"], ref["scale"])
+    ea = np.abs(a32.cpu().numpy().astype(np.float64) - ref["alpha"])
+    return {"queries": int(s.size), "fp32_comp_max_norm_err": float(e32.max()),
+            "fp32_comp_mean_norm_err": float(e32.mean()), "fp64_max_norm_err": float(e64.max()),
+            "alpha_max_abs_err": float(ea.max()),
+            "tolerance": {"fp32_comp": 1e-5, "fp64": 1e-9},
+            "measure": "max_q |z - z_oracle| / S_q, S_q = sum w|z| / sum w (oracle)"}
 
 
 def run_reference(args):
@@ -380,8 +408,12 @@ def run_ours(args):
                                   "dependent L2 gathers of the ring search, not by HBM"}
     stages_ms = {k: v[0] / args.steps for k, v in stage.items()}
     cpu = None
+    accuracy = None
     if not args.no_cpu_baseline and world >= 1:
-        cpu = cpu_baseline(w, args.cpu_seconds, rank)
+        cpu, sample, ref = cpu_baseline(w, args.cpu_seconds, rank, local=args.mode == "local")
+        if args.mode in ("aidw", "local"):
+            accuracy = accuracy_on_sample(binding, pkg, t, w, sample, ref, params,
+                                          args.mode == "local", out_z.cpu().numpy())
     metric = {"aidw": METRIC,
               "local": "local AIDW interpolated points/s at n=m=1M (kNN + Eq. 1 over the k nearest)",
               "knn": "grid build + kNN queries/s at n=m=1M (r_obs per query)"}[args.mode]
@@ -390,7 +422,7 @@ def run_ours(args):
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
             "data": "synthetic", "config": workload_config(args, world),
             "e2e": e2e, "gpu_launches": int(launches), "roofline": roofline,
-            "cpu_baseline": cpu, "fp64_plain": fp64,
+            "cpu_baseline": cpu, "accuracy": accuracy, "fp64_plain": fp64,
             "stages_ms_per_step": stages_ms, "wall_s_timed": wall,
             "clocks": clk, "device": props.name}
     print(json.dumps(line), flush=True)

@@ -122,6 +122,8 @@ def load(path: str | None = None):
         lib.aidw_knn_bruteforce.argtypes = [vp, vp, vp, i64, c_int, vp, vp, vp, vp]
         lib.aidw_interpolate_local.restype = c_int
         lib.aidw_interpolate_local.argtypes = [vp, vp, vp, i64, P(CParams), vp, vp, vp]
+        lib.aidw_test_expire_next_wait.restype = c_int
+        lib.aidw_test_expire_next_wait.argtypes = [c_int]
         lib.aidw_set_memory_limit.restype = c_int
         lib.aidw_set_memory_limit.argtypes = [i64, P(i64)]
         lib.aidw_profile_enable.restype = c_int
@@ -324,6 +326,11 @@ def aidw_interpolate_local(grid: Grid, qx, qy, params: Params | None = None, out
                                          _ptr(out_z), _ptr(out_alpha), _stream(stream)),
            "aidw_interpolate_local")
     return out_z, out_alpha
+
+
+def aidw_test_expire_next_wait(ms: int = 50) -> None:
+    """Test hook: the next weighting launch's bounded wait expires after ms."""
+    _check(load().aidw_test_expire_next_wait(int(ms)), "aidw_test_expire_next_wait")
 
 
 def aidw_set_memory_limit(nbytes: int) -> int:

@@ -454,6 +454,13 @@ aidw_status aidw_set_memory_limit(int64_t bytes, int64_t *held)
     return AIDW_OK;
 }
 
+aidw_status aidw_test_expire_next_wait(int ms)
+{
+    if (ms < 1 || ms > 2000) return AIDW_ERR_INVALID_ARG;
+    weight_expire_next_wait(ms);
+    return AIDW_OK;
+}
+
 aidw_status aidw_profile_enable(int on)
 {
     std::lock_guard<std::mutex> lk(g_prof_mu);

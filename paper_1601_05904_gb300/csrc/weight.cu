@@ -52,7 +52,7 @@ static_assert(kDTile == kWeightTile, "weighting tiles are staged whole");
 constexpr int kStages = 3;
 constexpr int kChunk = 32;     // points per plain float32 partial sum (per lane)
 constexpr int kChunk2 = 2 * kChunk;
-constexpr int kWaitTries = 4000;
+constexpr long long kWaitNs = 2000000000LL;  // a data-tile wait gives up after 2 s
 
 template <bool F64>
 struct WCfg;
@@ -94,6 +94,9 @@ struct SKArgs {
     long long G;        // CTAs
     long long total_q;  // queries of all jobs
     int *status;
+    long long wait_ns;  // bound of every mbarrier wait (nanoseconds)
+    long long skip_unit;  // test hook: the data tile of this unit is never
+                          // copied, so its wait expires (-1: none)
 };
 
 __device__ __forceinline__ WJob job_of_unit(const SKArgs &a, long long u)
@@ -142,6 +145,7 @@ __device__ __forceinline__ int aos_count(long long n_pad, long long d)
 __device__ __forceinline__ void issue_tile_soa(const SKArgs &a, float *buf, uint64_t *bar,
                                                long long u)
 {
+    if (u == a.skip_unit) return;
     const WJob J = job_of_unit(a, u);
     const long long d = (u - J.unit_base) % J.D;
     const uint32_t bytes = (uint32_t)soa_count(J.n_data, d) * 4u;
@@ -155,6 +159,7 @@ __device__ __forceinline__ void issue_tile_soa(const SKArgs &a, float *buf, uint
 __device__ __forceinline__ void issue_tile_aos(const SKArgs &a, Point *buf, uint64_t *bar,
                                                long long u)
 {
+    if (u == a.skip_unit) return;
     const WJob J = job_of_unit(a, u);
     const long long d = (u - J.unit_base) % J.D;
     const uint32_t bytes = (uint32_t)aos_count(J.n_pad, d) * (uint32_t)sizeof(Point);
@@ -230,7 +235,7 @@ __global__ void __launch_bounds__(THREADS, MINB)
         for (; u < seg_end; ++u) {
             const int s = (int)((u - u0) % kStages);
             const uint32_t par = (uint32_t)(((u - u0) / kStages) & 1);
-            const bool ok = mbar_wait_bounded(&full[s], par, kWaitTries);
+            const bool ok = mbar_wait_bounded(&full[s], par, a.wait_ns);
             const float *X = buf + s * 3 * kDTile;
             const float *Y = X + kDTile;
             const float *Z = Y + kDTile;
@@ -286,7 +291,7 @@ __global__ void __launch_bounds__(THREADS, MINB)
                 if (threadIdx.x == 0)
                     for (long long v = u; v < min(u1, u + kStages); ++v)
                         mbar_wait_bounded(&full[(v - u0) % kStages],
-                                          (uint32_t)(((v - u0) / kStages) & 1), kWaitTries);
+                                          (uint32_t)(((v - u0) / kStages) & 1), a.wait_ns);
                 __syncthreads();
                 return;
             }
@@ -389,7 +394,7 @@ __global__ void __launch_bounds__(WCfg<true>::kThreads, WCfg<true>::kMinBlocks)
         for (; u < seg_end; ++u) {
             const int s = (int)((u - u0) % kStages);
             const uint32_t par = (uint32_t)(((u - u0) / kStages) & 1);
-            const bool ok = mbar_wait_bounded(&full[s], par, kWaitTries);
+            const bool ok = mbar_wait_bounded(&full[s], par, a.wait_ns);
             const Point *tile = buf + s * kDTile;
             const int cnt = aos_count(J.n_pad, (u - J.unit_base) % J.D);
             if (ok) {
@@ -408,7 +413,7 @@ __global__ void __launch_bounds__(WCfg<true>::kThreads, WCfg<true>::kMinBlocks)
                 if (threadIdx.x == 0)
                     for (long long v = u; v < min(u1, u + kStages); ++v)
                         mbar_wait_bounded(&full[(v - u0) % kStages],
-                                          (uint32_t)(((v - u0) / kStages) & 1), kWaitTries);
+                                          (uint32_t)(((v - u0) / kStages) & 1), a.wait_ns);
                 __syncthreads();
                 return;
             }
@@ -501,10 +506,28 @@ int resident_ctas(int device)
     return c;
 }
 
+// Test hook (aidw_test_expire_next_wait): the next weighting launch skips
+// the copy of its first unit's data tile and bounds its waits at the given
+// number of milliseconds, so the wait expires and the timeout path runs.
+std::mutex g_hook_mu;
+int g_hook_ms = 0;
+
 // Launches the weighting kernel and the finalize kernel for the jobs in a.
 template <bool F64>
-aidw_status launch(const SKArgs &a, void *part, cudaStream_t s)
+aidw_status launch(SKArgs a, void *part, cudaStream_t s)
 {
+    a.wait_ns = kWaitNs;
+    a.skip_unit = -1;
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    if (cudaStreamIsCapturing(s, &cs) != cudaSuccess) cudaGetLastError();
+    if (cs == cudaStreamCaptureStatusNone) {  // never bake the hook into a graph
+        std::lock_guard<std::mutex> lk(g_hook_mu);
+        if (g_hook_ms > 0) {
+            a.wait_ns = 1000000LL * g_hook_ms;
+            a.skip_unit = 0;
+            g_hook_ms = 0;
+        }
+    }
     using C = WCfg<F64>;
     using Part = typename C::Part;
     const size_t smem = stage_smem<F64>();
@@ -590,6 +613,12 @@ aidw_status run_scratch(const aidw_grid *g, const float *qx, const float *qy, lo
 }
 
 }  // namespace
+
+void weight_expire_next_wait(int ms)
+{
+    std::lock_guard<std::mutex> lk(g_hook_mu);
+    g_hook_ms = ms;
+}
 
 long long weight_data_tiles(long long n_data, long long n_pad, bool fp64)
 {

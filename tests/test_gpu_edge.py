@@ -196,3 +196,21 @@ def test_interpolate_replays_in_a_cuda_graph(aidw, oracle):
         assert err.max() <= TOL_FP32
     del graph
     g.destroy()
+
+
+def test_expired_wait_reports_timeout_and_gpu_stays_usable(aidw, oracle):
+    """The weighting kernel's bounded data-tile wait: a copy that is never
+    issued makes the wait expire (50 ms); the kernel latches the timeout,
+    drains its own copies and returns; the next call is correct."""
+    w = inputs.uniform_kilo(n=20000, m=3000, seed=64)
+    p = aidw.Params(k=10)
+    g = aidw.aidw_grid_build(dev(w.x), dev(w.y), dev(w.z), p)
+    aidw.aidw_test_expire_next_wait(50)
+    aidw.aidw_interpolate(g, dev(w.qx), dev(w.qy), p)
+    assert aidw.aidw_grid_status(g) == 6          # AIDW_ERR_TIMEOUT
+    assert aidw.aidw_grid_status(g) == 0          # cleared
+    z, _ = aidw.aidw_interpolate(g, dev(w.qx), dev(w.qy), p)
+    assert aidw.aidw_grid_status(g) == 0
+    ref = oracle.aidw(w.x, w.y, w.z, w.qx, w.qy, 10)
+    assert oracle.normalized_error(host(z), ref["z"], ref["scale"]).max() <= TOL_FP32
+    g.destroy()
