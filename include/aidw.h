@@ -276,15 +276,16 @@ aidw_status aidw_set_memory_limit(int64_t bytes, int64_t *held);
 
 /* Test hook for the device-side timeout path (no counterpart in the paper).
  * Every wait of the weighting kernel for a shared-memory data tile is
- * bounded (2 s of wall time).  After this call the next weighting launch
- * (aidw_interpolate, the no-alloc form or a batch run) leaves the copy of
- * one data tile unissued and bounds its waits at `ms` (1..2000)
- * milliseconds (a launch being captured into a graph leaves the hook for
- * the next one), so the CTA that needs that tile gives up: it latches
- * AIDW_ERR_TIMEOUT, waits (bounded) for its own copies in flight and
- * returns.  The GPU stays usable; that call's predictions are undefined;
- * aidw_grid_status (or aidw_batch_plan_status) reports the timeout. */
-aidw_status aidw_test_expire_next_wait(int ms);
+ * bounded: at most 2000 tries, each suspending for up to ~1 ms.  After this
+ * call the next weighting launch (aidw_interpolate, the no-alloc form or a
+ * batch run; a launch being captured into a graph leaves the hook for the
+ * next one) leaves the copy of one data tile unissued and bounds its waits
+ * at `tries` (1..2000) tries, so the CTA that needs that tile gives up: it
+ * latches AIDW_ERR_TIMEOUT, waits (bounded) for its own copies in flight
+ * and returns.  The GPU stays usable; that call's predictions are
+ * undefined; aidw_grid_status (or aidw_batch_plan_status) reports the
+ * timeout. */
+aidw_status aidw_test_expire_next_wait(int tries);
 
 /* Short English name of a status code (static storage). */
 const char *aidw_status_string(aidw_status s);

@@ -328,9 +328,9 @@ def aidw_interpolate_local(grid: Grid, qx, qy, params: Params | None = None, out
     return out_z, out_alpha
 
 
-def aidw_test_expire_next_wait(ms: int = 50) -> None:
-    """Test hook: the next weighting launch's bounded wait expires after ms."""
-    _check(load().aidw_test_expire_next_wait(int(ms)), "aidw_test_expire_next_wait")
+def aidw_test_expire_next_wait(tries: int = 50) -> None:
+    """Test hook: the next weighting launch's bounded wait expires after tries."""
+    _check(load().aidw_test_expire_next_wait(int(tries)), "aidw_test_expire_next_wait")
 
 
 def aidw_set_memory_limit(nbytes: int) -> int:

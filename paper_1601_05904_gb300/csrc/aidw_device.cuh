@@ -249,25 +249,13 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, uint32_t parity)
     return ok != 0;
 }
 
-__device__ __forceinline__ unsigned long long global_ns()
+// Bounded wait: at most max_tries tries, each of which may suspend the
+// thread for up to the 1 ms hint while the phase is incomplete.
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t *bar, uint32_t parity, int max_tries)
 {
-    unsigned long long t;
-    asm volatile("mov.u64 %0, %globaltimer;" : "=l"(t));
-    return t;
-}
-
-// Bounded wait: tries until the phase completes or budget_ns of wall time
-// (the global nanosecond timer) have passed; each try may suspend up to the
-// 1 ms hint.
-__device__ __forceinline__ bool mbar_wait_bounded(uint64_t *bar, uint32_t parity,
-                                                  long long budget_ns)
-{
-    if (mbar_try_wait(bar, parity)) return true;
-    const unsigned long long t0 = global_ns();
-    for (;;) {
+    for (int i = 0; i < max_tries; ++i)
         if (mbar_try_wait(bar, parity)) return true;
-        if ((long long)(global_ns() - t0) > budget_ns) return false;
-    }
+    return false;
 }
 
 }  // namespace aidw

@@ -166,8 +166,8 @@ aidw_status weight_launch_batch(const WJob *jobs, int n_jobs, long long total_u,
                                 int *status, int device, cudaStream_t s);
 size_t weight_partial_bytes(bool fp64);  // bytes of one query tile's partials
 // Test hook: the next weighting launch leaves one data-tile copy unissued and
-// bounds its waits at `ms` milliseconds, so a wait expires.
-void weight_expire_next_wait(int ms);
+// bounds its waits at `tries` tries, so a wait expires.
+void weight_expire_next_wait(int tries);
 
 // Weighting (stream-K over all data points) + finalize.  Allocates its
 // partial-sum scratch with cudaMallocAsync on s.

@@ -454,10 +454,10 @@ aidw_status aidw_set_memory_limit(int64_t bytes, int64_t *held)
     return AIDW_OK;
 }
 
-aidw_status aidw_test_expire_next_wait(int ms)
+aidw_status aidw_test_expire_next_wait(int tries)
 {
-    if (ms < 1 || ms > 2000) return AIDW_ERR_INVALID_ARG;
-    weight_expire_next_wait(ms);
+    if (tries < 1 || tries > 2000) return AIDW_ERR_INVALID_ARG;
+    weight_expire_next_wait(tries);
     return AIDW_OK;
 }
 

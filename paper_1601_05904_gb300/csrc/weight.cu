@@ -52,7 +52,7 @@ static_assert(kDTile == kWeightTile, "weighting tiles are staged whole");
 constexpr int kStages = 3;
 constexpr int kChunk = 32;     // points per plain float32 partial sum (per lane)
 constexpr int kChunk2 = 2 * kChunk;
-constexpr long long kWaitNs = 2000000000LL;  // a data-tile wait gives up after 2 s
+constexpr int kWaitTries = 2000;  // tries of up to ~1 ms: a data-tile wait gives up after ~2 s
 
 template <bool F64>
 struct WCfg;
@@ -94,7 +94,7 @@ struct SKArgs {
     long long G;        // CTAs
     long long total_q;  // queries of all jobs
     int *status;
-    long long wait_ns;  // bound of every mbarrier wait (nanoseconds)
+    int wait_tries;     // bound of every mbarrier wait (tries; hook launches only)
     long long skip_unit;  // test hook: the data tile of this unit is never
                           // copied, so its wait expires (-1: none)
 };
@@ -142,10 +142,11 @@ __device__ __forceinline__ int aos_count(long long n_pad, long long d)
     return (int)min((long long)kDTile, n_pad - d * kDTile);
 }
 
+template <bool HOOK>
 __device__ __forceinline__ void issue_tile_soa(const SKArgs &a, float *buf, uint64_t *bar,
                                                long long u)
 {
-    if (u == a.skip_unit) return;
+    if (HOOK && u == a.skip_unit) return;
     const WJob J = job_of_unit(a, u);
     const long long d = (u - J.unit_base) % J.D;
     const uint32_t bytes = (uint32_t)soa_count(J.n_data, d) * 4u;
@@ -156,10 +157,11 @@ __device__ __forceinline__ void issue_tile_soa(const SKArgs &a, float *buf, uint
     bulk_g2s(buf + 2 * kDTile, src + 2 * kDTile, bytes, bar);
 }
 
+template <bool HOOK>
 __device__ __forceinline__ void issue_tile_aos(const SKArgs &a, Point *buf, uint64_t *bar,
                                                long long u)
 {
-    if (u == a.skip_unit) return;
+    if (HOOK && u == a.skip_unit) return;
     const WJob J = job_of_unit(a, u);
     const long long d = (u - J.unit_base) % J.D;
     const uint32_t bytes = (uint32_t)aos_count(J.n_pad, d) * (uint32_t)sizeof(Point);
@@ -179,11 +181,14 @@ __device__ __forceinline__ void issue_tile_aos(const SKArgs &a, Point *buf, uint
 // is the bound; moving part of the exp2s to the FMA pipe balances the two.
 // Measured on GB300 at n = m = 1M: 0/8 367 ms, 2/8 353 ms, 3/8 377 ms,
 // 4/8 395 ms, so 2/8 is the default.
-template <int POLY, int THREADS = WCfg<false>::kThreads, int Q = WCfg<false>::kQPT,
-          int MINB = WCfg<false>::kMinBlocks>
+// HOOK: the instantiation launched only while the timeout test hook is armed
+// (aidw_test_expire_next_wait); the normal kernel has no trace of it.
+template <int POLY, bool HOOK = false, int THREADS = WCfg<false>::kThreads,
+          int Q = WCfg<false>::kQPT, int MINB = WCfg<false>::kMinBlocks>
 __global__ void __launch_bounds__(THREADS, MINB)
     k_weight_f32(SKArgs a, float4 *__restrict__ part)
 {
+    const int wait_tries = HOOK ? a.wait_tries : kWaitTries;
     using C = WCfg<false>;
     static_assert(THREADS * Q == C::kQTile, "a query tile is THREADS x Q queries");
     extern __shared__ __align__(128) unsigned char smem_raw[];
@@ -200,7 +205,7 @@ __global__ void __launch_bounds__(THREADS, MINB)
     __syncthreads();
     if (threadIdx.x == 0)
         for (int s = 0; s < kStages; ++s)
-            if (u0 + s < u1) issue_tile_soa(a, buf + s * 3 * kDTile, &full[s], u0 + s);
+            if (u0 + s < u1) issue_tile_soa<HOOK>(a, buf + s * 3 * kDTile, &full[s], u0 + s);
 
     const F2 zero2 = f2_pack(0.0f, 0.0f);
     long long u = u0;
@@ -235,7 +240,7 @@ __global__ void __launch_bounds__(THREADS, MINB)
         for (; u < seg_end; ++u) {
             const int s = (int)((u - u0) % kStages);
             const uint32_t par = (uint32_t)(((u - u0) / kStages) & 1);
-            const bool ok = mbar_wait_bounded(&full[s], par, a.wait_ns);
+            const bool ok = mbar_wait_bounded(&full[s], par, wait_tries);
             const float *X = buf + s * 3 * kDTile;
             const float *Y = X + kDTile;
             const float *Z = Y + kDTile;
@@ -291,12 +296,12 @@ __global__ void __launch_bounds__(THREADS, MINB)
                 if (threadIdx.x == 0)
                     for (long long v = u; v < min(u1, u + kStages); ++v)
                         mbar_wait_bounded(&full[(v - u0) % kStages],
-                                          (uint32_t)(((v - u0) / kStages) & 1), a.wait_ns);
+                                          (uint32_t)(((v - u0) / kStages) & 1), wait_tries);
                 __syncthreads();
                 return;
             }
             if (threadIdx.x == 0 && u + kStages < u1)
-                issue_tile_soa(a, buf + s * 3 * kDTile, &full[s], u + kStages);
+                issue_tile_soa<HOOK>(a, buf + s * 3 * kDTile, &full[s], u + kStages);
         }
 
         const long long slot = J.tile_base + t + cta;
@@ -350,9 +355,11 @@ __global__ void k_finalize_f32(SKArgs a, const float4 *__restrict__ part)
 // ---------------------------------------------------------------------------
 // float64 plain weighting
 // ---------------------------------------------------------------------------
+template <bool HOOK = false>
 __global__ void __launch_bounds__(WCfg<true>::kThreads, WCfg<true>::kMinBlocks)
     k_weight_f64(SKArgs a, double2 *__restrict__ part)
 {
+    const int wait_tries = HOOK ? a.wait_tries : kWaitTries;
     using C = WCfg<true>;
     extern __shared__ __align__(128) unsigned char smem_raw[];
     Point *buf = reinterpret_cast<Point *>(smem_raw);
@@ -368,7 +375,7 @@ __global__ void __launch_bounds__(WCfg<true>::kThreads, WCfg<true>::kMinBlocks)
     __syncthreads();
     if (threadIdx.x == 0)
         for (int s = 0; s < kStages; ++s)
-            if (u0 + s < u1) issue_tile_aos(a, buf + s * kDTile, &full[s], u0 + s);
+            if (u0 + s < u1) issue_tile_aos<HOOK>(a, buf + s * kDTile, &full[s], u0 + s);
 
     long long u = u0;
     while (u < u1) {
@@ -394,7 +401,7 @@ __global__ void __launch_bounds__(WCfg<true>::kThreads, WCfg<true>::kMinBlocks)
         for (; u < seg_end; ++u) {
             const int s = (int)((u - u0) % kStages);
             const uint32_t par = (uint32_t)(((u - u0) / kStages) & 1);
-            const bool ok = mbar_wait_bounded(&full[s], par, a.wait_ns);
+            const bool ok = mbar_wait_bounded(&full[s], par, wait_tries);
             const Point *tile = buf + s * kDTile;
             const int cnt = aos_count(J.n_pad, (u - J.unit_base) % J.D);
             if (ok) {
@@ -413,12 +420,12 @@ __global__ void __launch_bounds__(WCfg<true>::kThreads, WCfg<true>::kMinBlocks)
                 if (threadIdx.x == 0)
                     for (long long v = u; v < min(u1, u + kStages); ++v)
                         mbar_wait_bounded(&full[(v - u0) % kStages],
-                                          (uint32_t)(((v - u0) / kStages) & 1), a.wait_ns);
+                                          (uint32_t)(((v - u0) / kStages) & 1), wait_tries);
                 __syncthreads();
                 return;
             }
             if (threadIdx.x == 0 && u + kStages < u1)
-                issue_tile_aos(a, buf + s * kDTile, &full[s], u + kStages);
+                issue_tile_aos<HOOK>(a, buf + s * kDTile, &full[s], u + kStages);
         }
         const long long slot = J.tile_base + t + cta;
 #pragma unroll
@@ -491,14 +498,19 @@ int resident_ctas(int device)
     int sms = 1, per_sm = 1;
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, device);
     if (F64) {
-        cudaFuncSetAttribute(k_weight_f64, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_weight_f64, WCfg<true>::kThreads,
-                                                      smem);
+        cudaFuncSetAttribute(k_weight_f64<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)smem);
+        cudaFuncSetAttribute(k_weight_f64<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)smem);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_weight_f64<false>,
+                                                      WCfg<true>::kThreads, smem);
     } else {
         cudaFuncSetAttribute(k_weight_f32<0>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         cudaFuncSetAttribute(k_weight_f32<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         cudaFuncSetAttribute(k_weight_f32<3>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         cudaFuncSetAttribute(k_weight_f32<4>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        cudaFuncSetAttribute(k_weight_f32<2, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)smem);
         cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_weight_f32<2>,
                                                       WCfg<false>::kThreads, smem);
     }
@@ -508,24 +520,24 @@ int resident_ctas(int device)
 
 // Test hook (aidw_test_expire_next_wait): the next weighting launch skips
 // the copy of its first unit's data tile and bounds its waits at the given
-// number of milliseconds, so the wait expires and the timeout path runs.
+// number of tries, so the wait expires and the timeout path runs.
 std::mutex g_hook_mu;
-int g_hook_ms = 0;
+int g_hook_tries = 0;
 
 // Launches the weighting kernel and the finalize kernel for the jobs in a.
 template <bool F64>
 aidw_status launch(SKArgs a, void *part, cudaStream_t s)
 {
-    a.wait_ns = kWaitNs;
+    a.wait_tries = kWaitTries;
     a.skip_unit = -1;
     cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
     if (cudaStreamIsCapturing(s, &cs) != cudaSuccess) cudaGetLastError();
     if (cs == cudaStreamCaptureStatusNone) {  // never bake the hook into a graph
         std::lock_guard<std::mutex> lk(g_hook_mu);
-        if (g_hook_ms > 0) {
-            a.wait_ns = 1000000LL * g_hook_ms;
+        if (g_hook_tries > 0) {
+            a.wait_tries = g_hook_tries;
             a.skip_unit = 0;
-            g_hook_ms = 0;
+            g_hook_tries = 0;
         }
     }
     using C = WCfg<F64>;
@@ -533,7 +545,12 @@ aidw_status launch(SKArgs a, void *part, cudaStream_t s)
     const size_t smem = stage_smem<F64>();
     int prof = profile_begin(s);
     if (F64) {
-        k_weight_f64<<<(unsigned)a.G, C::kThreads, smem, s>>>(a, static_cast<double2 *>(part));
+        if (a.skip_unit >= 0)
+            k_weight_f64<true><<<(unsigned)a.G, C::kThreads, smem, s>>>(a, static_cast<double2 *>(part));
+        else
+            k_weight_f64<<<(unsigned)a.G, C::kThreads, smem, s>>>(a, static_cast<double2 *>(part));
+    } else if (a.skip_unit >= 0) {
+        k_weight_f32<2, true><<<(unsigned)a.G, C::kThreads, smem, s>>>(a, static_cast<float4 *>(part));
     } else {
         float4 *pf = static_cast<float4 *>(part);
         switch (poly_units()) {
@@ -614,10 +631,10 @@ aidw_status run_scratch(const aidw_grid *g, const float *qx, const float *qy, lo
 
 }  // namespace
 
-void weight_expire_next_wait(int ms)
+void weight_expire_next_wait(int tries)
 {
     std::lock_guard<std::mutex> lk(g_hook_mu);
-    g_hook_ms = ms;
+    g_hook_tries = tries;
 }
 
 long long weight_data_tiles(long long n_data, long long n_pad, bool fp64)

@@ -200,7 +200,7 @@ def test_interpolate_replays_in_a_cuda_graph(aidw, oracle):
 
 def test_expired_wait_reports_timeout_and_gpu_stays_usable(aidw, oracle):
     """The weighting kernel's bounded data-tile wait: a copy that is never
-    issued makes the wait expire (50 ms); the kernel latches the timeout,
+    issued makes the wait expire (50 tries); the kernel latches the timeout,
     drains its own copies and returns; the next call is correct."""
     w = inputs.uniform_kilo(n=20000, m=3000, seed=64)
     p = aidw.Params(k=10)
