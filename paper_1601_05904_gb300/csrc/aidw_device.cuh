@@ -152,6 +152,45 @@ __device__ __forceinline__ F2 f2_exp2_poly(F2 t)
     return f2_pack(w0, w1);
 }
 
+// log2 of two positive float32 lanes on the FMA pipe, the counterpart of
+// f2_exp2_poly for moving lg2 work off the SFU (which evaluates lg2 at half
+// its ex2 rate).  Reduction x = 2^e * m with m in [sqrt(1/2), sqrt(2)):
+// with i = bits(x) - bits(sqrt(1/2)), e = i >> 23 (arithmetic shift) and m
+// has the bits (i & 0x7FFFFF) + bits(sqrt(1/2)), so both come from integer
+// operations; e becomes a float by the 1.5 * 2^23 exponent-field trick.  With
+// s = m - 1 in [-0.293, 0.415), log2(1 + s) = s * P(s), P of degree 7 fitted
+// to minimise the absolute error (Lawson-iterated weighted least squares;
+// 4.8e-8 before rounding, 1.0e-7 when evaluated in float32 on [1/2, 2],
+// inside the 2^-22.6 bound of lg2.approx).  +inf maps to +inf, so padding
+// points keep weight 0; x = 0 gives -127 (zero distances are never weighted:
+// such queries are replaced in the finalize step).
+__device__ __forceinline__ F2 f2_log2_poly(F2 x)
+{
+    float x0, x1;
+    f2_unpack(x, x0, x1);
+    const int b0 = __float_as_int(x0), b1 = __float_as_int(x1);
+    const int i0 = b0 - 0x3F3504F3, i1 = b1 - 0x3F3504F3;
+    const F2 m = f2_pack(__int_as_float((i0 & 0x007FFFFF) + 0x3F3504F3),
+                         __int_as_float((i1 & 0x007FFFFF) + 0x3F3504F3));
+    const F2 magic = f2_pack(12582912.0f, 12582912.0f);  // 1.5 * 2^23
+    const F2 e = f2_sub(f2_pack(__int_as_float((i0 >> 23) + 0x4B400000),
+                                __int_as_float((i1 >> 23) + 0x4B400000)),
+                        magic);
+    const F2 s = f2_sub(m, f2_pack(1.0f, 1.0f));
+    F2 p = f2_fma(f2_pack(-1.4574451744556427e-01f, -1.4574451744556427e-01f), s,
+                  f2_pack(2.3689043521881104e-01f, 2.3689043521881104e-01f));
+    p = f2_fma(p, s, f2_pack(-2.500690519809723e-01f, -2.500690519809723e-01f));
+    p = f2_fma(p, s, f2_pack(2.8670746088027954e-01f, 2.8670746088027954e-01f));
+    p = f2_fma(p, s, f2_pack(-3.6008721590042114e-01f, -3.6008721590042114e-01f));
+    p = f2_fma(p, s, f2_pack(4.8093944787979126e-01f, 4.8093944787979126e-01f));
+    p = f2_fma(p, s, f2_pack(-7.213571667671204e-01f, -7.213571667671204e-01f));
+    p = f2_fma(p, s, f2_pack(1.4426947832107544e+00f, 1.4426947832107544e+00f));
+    float l0, l1;
+    f2_unpack(f2_fma(s, p, e), l0, l1);
+    const float inf = __int_as_float(0x7f800000);
+    return f2_pack(b0 >= 0x7F800000 ? inf : l0, b1 >= 0x7F800000 ? inf : l1);
+}
+
 // Error-free transformation (Knuth's TwoSum): s + e == a + b exactly.
 __device__ __forceinline__ void two_sum(float a, float b, float &s, float &e)
 {

@@ -37,6 +37,7 @@
 #include <string.h>
 
 #include <algorithm>
+#include <cstdio>
 #include <mutex>
 #include <type_traits>
 
@@ -175,15 +176,14 @@ __device__ __forceinline__ void issue_tile_aos(const SKArgs &a, Point *buf, uint
 // Each thread holds kQPT queries; every packed instruction applies one query
 // to two consecutive data points (lanes), so a 16-byte shared load of the
 // tile's x (or y, z) array feeds two packed operands.
-// POLY: how many of the 2 x kQPT (point pair, query) products of one inner
-// step take exp2 from the FMA-pipe polynomial instead of the SFU.  The SFU
+// PE, PL: how many of the 2 x kQPT (point pair, query) products of one inner
+// step take exp2 (PE, counted from the first product) and lg2 (PL, counted
+// from the last) from FMA-pipe polynomials instead of the SFU.  The SFU
 // evaluates lg2 at half the rate of ex2, so with one of each per pair the SFU
-// is the bound; moving part of the exp2s to the FMA pipe balances the two.
-// Measured on GB300 at n = m = 1M: 0/8 367 ms, 2/8 353 ms, 3/8 377 ms,
-// 4/8 395 ms, so 2/8 is the default.
+// is the bound; moving part of the work to the FMA pipe balances the two.
 // HOOK: the instantiation launched only while the timeout test hook is armed
 // (aidw_test_expire_next_wait); the normal kernel has no trace of it.
-template <int POLY, bool HOOK = false, int THREADS = WCfg<false>::kThreads,
+template <int PE, int PL, bool HOOK = false, int THREADS = WCfg<false>::kThreads,
           int Q = WCfg<false>::kQPT, int MINB = WCfg<false>::kMinBlocks>
 __global__ void __launch_bounds__(THREADS, MINB)
     k_weight_f32(SKArgs a, float4 *__restrict__ part)
@@ -265,12 +265,17 @@ __global__ void __launch_bounds__(THREADS, MINB)
                                 const F2 dx = f2_add(qx2[i], xs[h]);
                                 const F2 dy = f2_add(qy2[i], ys[h]);
                                 const F2 d2 = f2_fma(dy, dy, f2_mul(dx, dx));
-                                float d0, d1;
-                                f2_unpack(d2, d0, d1);
-                                const F2 tt =
-                                    f2_fma(f2_pack(lg2_sfu(d0), lg2_sfu(d1)), c2[i], b2[i]);
+                                F2 lg;
+                                if (h * Q + i >= 2 * Q - PL) {
+                                    lg = f2_log2_poly(d2);
+                                } else {
+                                    float d0, d1;
+                                    f2_unpack(d2, d0, d1);
+                                    lg = f2_pack(lg2_sfu(d0), lg2_sfu(d1));
+                                }
+                                const F2 tt = f2_fma(lg, c2[i], b2[i]);
                                 F2 w;
-                                if (h * Q + i < POLY) {
+                                if (h * Q + i < PE) {
                                     w = f2_exp2_poly(tt);
                                 } else {
                                     float t0, t1;
@@ -464,17 +469,33 @@ __global__ void k_finalize_f64(SKArgs a, const double2 *__restrict__ part)
     out_z[q] = swz / sw;
 }
 
-// Number of the 2 x kQPT products per inner step whose exp2 runs on the FMA
-// pipe (0, 2, 3 or 4; default 2).  AIDW_EXP2_POLY_UNITS overrides it, for
-// measuring the balance on a given GPU.
-int poly_units()
+// Polynomial split of the float32 kernel: products per inner step whose exp2
+// (first number) and lg2 (second) run on the FMA pipe.  Measured on GB300 at
+// n = m = 1M (weighting ms): {2,0} 353.9, {0,0} 367.9, {3,0} 377.5,
+// {4,0} 395, {0,1} 357.5, {1,1} 358.7, {0,2} 377.5, {2,1} 393.2, so {2,0} is
+// the default.  AIDW_WEIGHT_POLY ("E,L") selects another entry of the table,
+// for measuring the balance on a given GPU.
+using F32Kernel = void (*)(SKArgs, float4 *);
+struct PolySplit {
+    int e, l;
+    F32Kernel kernel;
+};
+const PolySplit kPolySplits[] = {
+    {2, 0, k_weight_f32<2, 0>}, {0, 0, k_weight_f32<0, 0>}, {3, 0, k_weight_f32<3, 0>},
+    {4, 0, k_weight_f32<4, 0>}, {0, 1, k_weight_f32<0, 1>}, {1, 1, k_weight_f32<1, 1>},
+    {0, 2, k_weight_f32<0, 2>}};
+constexpr int kNumPolySplits = (int)(sizeof(kPolySplits) / sizeof(kPolySplits[0]));
+F32Kernel f32_kernel()
 {
-    static const int v = [] {
-        const char *e = getenv("AIDW_EXP2_POLY_UNITS");
-        const int x = e ? atoi(e) : 2;
-        return (x == 0 || x == 2 || x == 3 || x == 4) ? x : 2;
+    static const F32Kernel k = [] {
+        const char *e = getenv("AIDW_WEIGHT_POLY");
+        int pe = -1, pl = -1;
+        if (e && sscanf(e, "%d,%d", &pe, &pl) == 2)
+            for (int i = 0; i < kNumPolySplits; ++i)
+                if (kPolySplits[i].e == pe && kPolySplits[i].l == pl) return kPolySplits[i].kernel;
+        return kPolySplits[0].kernel;
     }();
-    return v;
+    return k;
 }
 
 // Dynamic shared memory of the weighting kernels: kStages data tiles.
@@ -505,13 +526,12 @@ int resident_ctas(int device)
         cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_weight_f64<false>,
                                                       WCfg<true>::kThreads, smem);
     } else {
-        cudaFuncSetAttribute(k_weight_f32<0>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        cudaFuncSetAttribute(k_weight_f32<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        cudaFuncSetAttribute(k_weight_f32<3>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        cudaFuncSetAttribute(k_weight_f32<4>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        cudaFuncSetAttribute(k_weight_f32<2, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             (int)smem);
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_weight_f32<2>,
+        for (int i = 0; i < kNumPolySplits; ++i)
+            cudaFuncSetAttribute(kPolySplits[i].kernel,
+                                 cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        cudaFuncSetAttribute(k_weight_f32<2, 0, true>,
+                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, f32_kernel(),
                                                       WCfg<false>::kThreads, smem);
     }
     c = std::max(1, sms * std::max(1, per_sm));
@@ -550,15 +570,10 @@ aidw_status launch(SKArgs a, void *part, cudaStream_t s)
         else
             k_weight_f64<<<(unsigned)a.G, C::kThreads, smem, s>>>(a, static_cast<double2 *>(part));
     } else if (a.skip_unit >= 0) {
-        k_weight_f32<2, true><<<(unsigned)a.G, C::kThreads, smem, s>>>(a, static_cast<float4 *>(part));
+        k_weight_f32<2, 0, true><<<(unsigned)a.G, C::kThreads, smem, s>>>(a, static_cast<float4 *>(part));
     } else {
         float4 *pf = static_cast<float4 *>(part);
-        switch (poly_units()) {
-        case 0: k_weight_f32<0><<<(unsigned)a.G, C::kThreads, smem, s>>>(a, pf); break;
-        case 3: k_weight_f32<3><<<(unsigned)a.G, C::kThreads, smem, s>>>(a, pf); break;
-        case 4: k_weight_f32<4><<<(unsigned)a.G, C::kThreads, smem, s>>>(a, pf); break;
-        default: k_weight_f32<2><<<(unsigned)a.G, C::kThreads, smem, s>>>(a, pf); break;
-        }
+        f32_kernel()<<<(unsigned)a.G, C::kThreads, smem, s>>>(a, pf);
     }
     profile_end(prof, s, AIDW_STAGE_WEIGHT, 1);
     prof = profile_begin(s);
