@@ -27,6 +27,9 @@
  *                       box, cell width from Eq. 2, nCol/nRow, cell index
  *                       per point, points ordered by cell (stable), and the
  *                       (head, count) pair of every cell.
+ *   oracle_knn_paper_rule  Sec. 3.2.4 grid kNN with the paper's own stop
+ *                       rule (first level holding k points, plus one level),
+ *                       which is not always exact; kept to measure that.
  *
  * Readings of the paper that this oracle fixes (the paper is silent or
  * garbled there):
@@ -413,4 +416,86 @@ void oracle_grid_fill(const float *x, const float *y, int64_t n,
     for (int64_t c = 0; c < ncells; ++c) fill[c] = out_cell_start[c];
     for (int64_t i = 0; i < n; ++i) out_perm[fill[out_key[i]]++] = i;
     free(fill);
+}
+
+/* ---------------------------------------------------------------------- */
+/* Sec. 3.2.4 grid kNN with the paper's level rule.                        */
+/* ---------------------------------------------------------------------- */
+/* Number of points in the block of cells of level L around (col, row):
+ * columns col-L .. col+L and rows row-L .. row+L, clipped to the grid. */
+static int64_t oracle_block_count(const int64_t *cell_start, int64_t ncol, int64_t nrow,
+                                  int64_t col, int64_t row, int64_t L)
+{
+    const int64_t c0 = col - L < 0 ? 0 : col - L;
+    const int64_t c1 = col + L > ncol - 1 ? ncol - 1 : col + L;
+    const int64_t r0 = row - L < 0 ? 0 : row - L;
+    const int64_t r1 = row + L > nrow - 1 ? nrow - 1 : row + L;
+    int64_t cnt = 0;
+    for (int64_t r = r0; r <= r1; ++r)
+        cnt += cell_start[r * ncol + c1 + 1] - cell_start[r * ncol + c0];
+    return cnt;
+}
+
+/* The kNN search of Sec. 3.2.4 as the paper states it, on the grid of
+ * oracle_grid_dims / oracle_grid_fill (info, cell_start, perm):
+ *   Step 1  locate the query's cell (same floor-and-clamp as the points);
+ *   Step 2  the level of cell expanding: the smallest L whose block of
+ *           (2L+1)^2 cells holds at least k points, then one level more
+ *           (the remark on Fig. 4);
+ *   Step 3  the k nearest of the points in that block (every squared
+ *           distance, full sort by (d^2, original index), first k).
+ * The candidate set is a subset of all points, so the result can miss true
+ * neighbours; out_d[j] >= the exact j-th distance for every j.
+ * out_idx: [m * k] original indices; out_d: [m * k] distances. */
+void oracle_knn_paper_rule(const float *x, const float *y, int64_t n, const double *info,
+                           const int64_t *cell_start, const int64_t *perm,
+                           const float *qx, const float *qy, int64_t m, int k,
+                           int32_t *out_idx, double *out_d, int nthreads)
+{
+    const double minx = info[0], miny = info[1], cw = info[6];
+    const int64_t ncol = (int64_t)info[7], nrow = (int64_t)info[8];
+#ifdef _OPENMP
+    if (nthreads <= 0) nthreads = omp_get_max_threads();
+#pragma omp parallel num_threads(nthreads)
+#endif
+    {
+        oracle_pair *buf = (oracle_pair *)malloc((size_t)n * sizeof(oracle_pair));
+#ifdef _OPENMP
+#pragma omp for schedule(dynamic, 1)
+#endif
+        for (int64_t q = 0; q < m; ++q) {
+            const double px = (double)qx[q], py = (double)qy[q];
+            int64_t col = (int64_t)floor((px - minx) / cw);
+            int64_t row = (int64_t)floor((py - miny) / cw);
+            if (col < 0) col = 0;
+            if (col > ncol - 1) col = ncol - 1;
+            if (row < 0) row = 0;
+            if (row > nrow - 1) row = nrow - 1;
+            int64_t L = 0;
+            while (oracle_block_count(cell_start, ncol, nrow, col, row, L) < k) ++L;
+            L += 1;
+            const int64_t c0 = col - L < 0 ? 0 : col - L;
+            const int64_t c1 = col + L > ncol - 1 ? ncol - 1 : col + L;
+            const int64_t r0 = row - L < 0 ? 0 : row - L;
+            const int64_t r1 = row + L > nrow - 1 ? nrow - 1 : row + L;
+            int64_t cnt = 0;
+            for (int64_t r = r0; r <= r1; ++r)
+                for (int64_t s = cell_start[r * ncol + c0]; s < cell_start[r * ncol + c1 + 1];
+                     ++s) {
+                    const int64_t i = perm[s];
+                    const double dx = px - (double)x[i];
+                    const double dy = py - (double)y[i];
+                    buf[cnt].d2 = dx * dx + dy * dy;
+                    buf[cnt].idx = i;
+                    ++cnt;
+                }
+            qsort(buf, (size_t)cnt, sizeof(oracle_pair), oracle_pair_cmp);
+            for (int j = 0; j < k; ++j) {
+                out_idx[q * k + j] = (int32_t)buf[j].idx;
+                out_d[q * k + j] = sqrt(buf[j].d2);
+            }
+        }
+        free(buf);
+    }
+    (void)nthreads;
 }

@@ -345,3 +345,49 @@ def test_local_constant_field_and_hits(oracle):
     sel = np.arange(0, w.n, 41)
     out = oracle.aidw_local(w.x, w.y, w.z, w.x[sel], w.y[sel], 8)
     np.testing.assert_array_equal(out["z"], w.z[sel].astype(np.float64))
+
+
+# ---- grid kNN with the paper's level rule (Sec. 3.2.4) -------------------------
+PAPER_RULE_GOLDEN = os.path.join(os.path.dirname(__file__), "golden", "knn_paper_rule_cases.json")
+
+
+def _paper_rule_cases():
+    with open(PAPER_RULE_GOLDEN) as f:
+        return json.load(f)["cases"]
+
+
+@pytest.mark.parametrize("case", _paper_rule_cases(), ids=lambda c: c["name"])
+def test_paper_rule_hand_derived_cases(oracle, case):
+    g = oracle.grid(case["x"], case["y"], cell_scale=case["cell_scale"])
+    assert (g["cw"], g["ncol"], g["nrow"]) == (1.0, 11, 11)
+    idx, _ = oracle.knn_paper_rule(case["x"], case["y"], case["qx"], case["qy"], case["k"],
+                                   cell_scale=case["cell_scale"])
+    np.testing.assert_array_equal(idx, case["expected_paper_rule_idx"])
+    idx, _ = oracle.knn(case["x"], case["y"], case["qx"], case["qy"], case["k"])
+    np.testing.assert_array_equal(idx, case["expected_exact_idx"])
+
+
+@pytest.mark.parametrize("seed,cell_scale,k", [(0, 1.0, 10), (1, 0.5, 5), (2, 2.0, 20)])
+def test_paper_rule_never_beats_the_exact_knn(oracle, seed, cell_scale, k):
+    """The rule picks the k best of a subset of the points, so its j-th
+    distance is never below the exact j-th distance; where the two index
+    lists agree, the distances agree exactly."""
+    w = inputs.clustered_kilo(n=3000, m=800, k=k, seed=seed)
+    pi, pd = oracle.knn_paper_rule(w.x, w.y, w.qx, w.qy, k, cell_scale=cell_scale)
+    ei, ed = oracle.knn(w.x, w.y, w.qx, w.qy, k)
+    assert (pd >= ed).all()
+    same = (pi == ei).all(1)
+    np.testing.assert_array_equal(pd[same], ed[same])
+    assert same.mean() > 0.5
+
+
+def test_paper_rule_is_exact_when_the_block_covers_the_grid(oracle):
+    """With a few large cells the widened block is the whole grid, and the
+    rule reduces to the brute-force kNN."""
+    w = inputs.unit_square(200, m=300, seed=4)
+    g = oracle.grid(w.x, w.y, cell_scale=20.0)
+    assert g["ncol"] <= 2 and g["nrow"] <= 2     # level 1 spans the grid from any cell
+    pi, pd = oracle.knn_paper_rule(w.x, w.y, w.qx, w.qy, 7, cell_scale=20.0)
+    ei, ed = oracle.knn(w.x, w.y, w.qx, w.qy, 7)
+    np.testing.assert_array_equal(pi, ei)
+    np.testing.assert_array_equal(pd, ed)
