@@ -52,7 +52,7 @@ def parse():
     ap.add_argument("--no-tune", action="store_true", help="batch: skip the autotuner")
     ap.add_argument("--cell-scale", type=float, default=0.0,
                     help="grid cell width / r_exp (<= 0: the library's choice)")
-    ap.add_argument("--mode", choices=("aidw", "local", "knn", "knn-table", "sweep"),
+    ap.add_argument("--mode", choices=("aidw", "local", "knn", "knn-table", "sweep", "knn-rule"),
                     default="aidw",
                     help="aidw: Eq. 1 over all points; local: Eq. 1 over the k nearest; "
                          "knn-table: grid vs all-points kNN at the paper's sizes; "
@@ -582,6 +582,53 @@ def run_tables(args):
     return 0
 
 
+def run_knn_rule(args):
+    """How often the paper's level rule (Sec. 3.2.4: first level holding k
+    points, plus one) misses a true neighbour, against the exact grid kNN on
+    the same grid: share of queries whose k-nearest list differs, r_obs
+    (Eq. 3) error, and the time of both searches."""
+    import torch
+
+    import paper_1601_05904_gb300 as pkg
+    from paper_1601_05904_gb300 import binding, inputs
+
+    torch.cuda.set_device(0)
+    binding.load()
+    dev = torch.device("cuda", 0)
+    rows = []
+    for wname in ("uniform", "clustered"):
+        gen = inputs.uniform_kilo if wname == "uniform" else inputs.clustered_kilo
+        w = gen(n=args.n, k=args.k)
+        t = {a: torch.from_numpy(getattr(w, a)).to(dev) for a in ("x", "y", "z", "qx", "qy")}
+        for cs in (1.0, 0.0):
+            p = pkg.Params(k=w.k, cell_scale=cs)
+            g = binding.aidw_grid_build(t["x"], t["y"], t["z"], p)
+            ie, _, re_ = binding.aidw_knn(g, t["qx"], t["qy"], w.k)
+            ip, _, rp = binding.aidw_knn_paper_rule(g, t["qx"], t["qy"], w.k)
+            torch.cuda.synchronize()
+            differ = (ie != ip).any(dim=1)
+            rel = ((rp.double() - re_.double()) / re_.double().clamp_min(1e-300)).abs()
+            reps = max(1, args.steps)
+            ms_exact = _time_ms(lambda: binding.aidw_knn(g, t["qx"], t["qy"], w.k,
+                                                         want=("robs",)), reps)
+            ms_paper = _time_ms(lambda: binding.aidw_knn_paper_rule(g, t["qx"], t["qy"], w.k,
+                                                                    want=("robs",)), reps)
+            info = binding.aidw_grid_get_info(g)
+            assert binding.aidw_grid_status(g) == 0
+            g.destroy()
+            rows.append({"workload": wname, "cell_scale": info["cell_scale"],
+                         "cell_width": info["cell_width"],
+                         "queries_with_a_missed_neighbour": float(differ.double().mean()),
+                         "r_obs_rel_err_max": float(rel.max()),
+                         "r_obs_rel_err_mean": float(rel.mean()),
+                         "exact_knn_ms": ms_exact, "paper_rule_knn_ms": ms_paper})
+    print(json.dumps({"metric": "kNN misses of the paper's level rule vs the exact grid kNN",
+                      "n": args.n, "k": args.k, "data": "synthetic",
+                      "device": torch.cuda.get_device_properties(dev).name, "rows": rows}),
+          flush=True)
+    return 0
+
+
 def main():
     args = parse()
     if args.impl == "reference":
@@ -590,6 +637,8 @@ def main():
         return run_batch(args)
     if args.mode in ("knn-table", "sweep"):
         return run_tables(args)
+    if args.mode == "knn-rule":
+        return run_knn_rule(args)
     return run_ours(args)
 
 

@@ -256,6 +256,19 @@ aidw_status aidw_knn_bruteforce(const aidw_grid *g, const float *qx, const float
                                 int64_t n_query, int k, int32_t *out_idx, float *out_dist,
                                 float *out_robs, aidw_stream_t stream);
 
+/* The grid kNN with the paper's own stop rule (Sec. 3.2.4, Step 2 and the
+ * remark on Fig. 4): the level of cell expanding is the first L whose block
+ * of (2L+1)^2 cells (clipped to the grid) holds at least k points, and the
+ * search covers one level more, L+1; the result is the k nearest of the
+ * points in that block.  This is not always the exact kNN (a point just
+ * outside the widened block can be nearer than the k-th point inside it);
+ * aidw_knn is exact.  Kept to measure how often the paper's rule misses.
+ * Same arguments, outputs, float32 distances, (distance, index) order and
+ * error behaviour as aidw_knn; distances are never below aidw_knn's. */
+aidw_status aidw_knn_paper_rule(const aidw_grid *g, const float *qx, const float *qy,
+                                int64_t n_query, int k, int32_t *out_idx, float *out_dist,
+                                float *out_robs, aidw_stream_t stream);
+
 /* Local AIDW: alpha exactly as aidw_interpolate (Eq. 2-6 from the k nearest
  * neighbours), but the weighted average of Eq. 1 taken over those k
  * neighbours only (n = k in Eq. 1's "data points used in interpolating")

@@ -97,7 +97,8 @@ def _load():
                                    c_i32, c_d, ctypes.c_int]
         lib.oracle_knn_paper_rule.restype = None
         lib.oracle_knn_paper_rule.argtypes = [c_f, c_f, i64, c_d, c_i64, c_i64, c_f, c_f, i64,
-                                              ctypes.c_int, c_i32, c_d, ctypes.c_int]
+                                              ctypes.c_int, ctypes.c_int, c_i32, c_d,
+                                              ctypes.c_int]
         lib.oracle_aidw.restype = None
         lib.oracle_aidw.argtypes = [c_f, c_f, c_f, i64, c_f, c_f, i64, ctypes.c_int,
                                     c_d, ctypes.c_double, ctypes.c_double,
@@ -174,12 +175,13 @@ def knn(x, y, qx, qy, k: int, nthreads: int = 0):
 
 
 def knn_paper_rule(x, y, qx, qy, k: int, cell_scale: float = 1.0, area: float = 0.0,
-                   cw_override: float = 0.0, nthreads: int = 0):
+                   cw_override: float = 0.0, n_out: int | None = None, nthreads: int = 0):
     """Grid kNN with the paper's level rule (Sec. 3.2.4: the first level of
     cell expanding whose block holds k points, plus one level), on the grid
-    of ``grid`` with the same arguments.  Returns (idx int32 [m,k], dist f64
-    [m,k]) in increasing (distance, index) order among the block's points;
-    not always the exact kNN."""
+    of ``grid`` with the same arguments.  Returns (idx int32 [m,n_out], dist
+    f64 [m,n_out]), the block's points in increasing (distance, index)
+    order; k fixes the level, n_out >= k (default k) columns are returned
+    (-1 / inf past the block's count).  Not always the exact kNN."""
     x, y, qx, qy = _f32(x), _f32(y), _f32(qx), _f32(qy)
     n, m = x.size, qx.size
     if not (1 <= k <= n):
@@ -196,13 +198,16 @@ def knn_paper_rule(x, y, qx, qy, k: int, cell_scale: float = 1.0, area: float = 
     lib.oracle_grid_fill(_ptr(x, ctypes.c_float), _ptr(y, ctypes.c_float), n,
                          _ptr(info, ctypes.c_double), _ptr(key, ctypes.c_int64),
                          _ptr(start, ctypes.c_int64), _ptr(perm, ctypes.c_int64))
-    idx = np.empty((m, k), dtype=np.int32)
-    dist = np.empty((m, k), dtype=np.float64)
+    n_out = k if n_out is None else int(n_out)
+    if n_out < k:
+        raise ValueError("need n_out >= k")
+    idx = np.empty((m, n_out), dtype=np.int32)
+    dist = np.empty((m, n_out), dtype=np.float64)
     if m:
         lib.oracle_knn_paper_rule(_ptr(x, ctypes.c_float), _ptr(y, ctypes.c_float), n,
                                   _ptr(info, ctypes.c_double), _ptr(start, ctypes.c_int64),
                                   _ptr(perm, ctypes.c_int64), _ptr(qx, ctypes.c_float),
-                                  _ptr(qy, ctypes.c_float), m, int(k),
+                                  _ptr(qy, ctypes.c_float), m, int(k), n_out,
                                   _ptr(idx, ctypes.c_int32), _ptr(dist, ctypes.c_double),
                                   int(nthreads))
     return idx, dist

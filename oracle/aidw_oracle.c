@@ -446,10 +446,13 @@ static int64_t oracle_block_count(const int64_t *cell_start, int64_t ncol, int64
  *           distance, full sort by (d^2, original index), first k).
  * The candidate set is a subset of all points, so the result can miss true
  * neighbours; out_d[j] >= the exact j-th distance for every j.
- * out_idx: [m * k] original indices; out_d: [m * k] distances. */
+ * k fixes the level; the first k_out >= k candidates of the block are
+ * written (index -1 and +inf beyond the block's point count), so a caller
+ * can see the gap after the k-th.
+ * out_idx: [m * k_out] original indices; out_d: [m * k_out] distances. */
 void oracle_knn_paper_rule(const float *x, const float *y, int64_t n, const double *info,
                            const int64_t *cell_start, const int64_t *perm,
-                           const float *qx, const float *qy, int64_t m, int k,
+                           const float *qx, const float *qy, int64_t m, int k, int k_out,
                            int32_t *out_idx, double *out_d, int nthreads)
 {
     const double minx = info[0], miny = info[1], cw = info[6];
@@ -490,9 +493,9 @@ void oracle_knn_paper_rule(const float *x, const float *y, int64_t n, const doub
                     ++cnt;
                 }
             qsort(buf, (size_t)cnt, sizeof(oracle_pair), oracle_pair_cmp);
-            for (int j = 0; j < k; ++j) {
-                out_idx[q * k + j] = (int32_t)buf[j].idx;
-                out_d[q * k + j] = sqrt(buf[j].d2);
+            for (int j = 0; j < k_out; ++j) {
+                out_idx[q * k_out + j] = j < cnt ? (int32_t)buf[j].idx : -1;
+                out_d[q * k_out + j] = j < cnt ? sqrt(buf[j].d2) : INFINITY;
             }
         }
         free(buf);

@@ -120,6 +120,8 @@ def load(path: str | None = None):
         lib.aidw_interpolate.argtypes = [vp, vp, vp, i64, P(CParams), vp, vp, vp]
         lib.aidw_knn_bruteforce.restype = c_int
         lib.aidw_knn_bruteforce.argtypes = [vp, vp, vp, i64, c_int, vp, vp, vp, vp]
+        lib.aidw_knn_paper_rule.restype = c_int
+        lib.aidw_knn_paper_rule.argtypes = [vp, vp, vp, i64, c_int, vp, vp, vp, vp]
         lib.aidw_interpolate_local.restype = c_int
         lib.aidw_interpolate_local.argtypes = [vp, vp, vp, i64, P(CParams), vp, vp, vp]
         lib.aidw_test_expire_next_wait.restype = c_int
@@ -245,10 +247,7 @@ def aidw_grid_status(grid: Grid) -> int:
     return int(load().aidw_grid_status(grid.handle))
 
 
-def aidw_knn(grid: Grid, qx, qy, k: int, out_idx=None, out_dist=None, out_robs=None,
-             want=("idx", "dist", "robs"), stream=None):
-    """Grid kNN.  Allocates the outputs named in ``want`` that are not given.
-    Returns (idx int32 [m,k] | None, dist float32 [m,k] | None, robs float32 [m] | None)."""
+def _knn_call(name: str, grid: Grid, qx, qy, k: int, out_idx, out_dist, out_robs, want, stream):
     import torch
     qx, qy = _f32_dev(qx, "qx"), _f32_dev(qy, "qy")
     m = qx.numel()
@@ -260,28 +259,32 @@ def aidw_knn(grid: Grid, qx, qy, k: int, out_idx=None, out_dist=None, out_robs=N
         out_dist = torch.empty((m, k), dtype=torch.float32, device=qx.device)
     if out_robs is None and "robs" in want:
         out_robs = torch.empty(m, dtype=torch.float32, device=qx.device)
-    _check(load().aidw_knn(grid.handle, _ptr(qx), _ptr(qy), m, int(k), _ptr(out_idx),
-                           _ptr(out_dist), _ptr(out_robs), _stream(stream)), "aidw_knn")
+    _check(getattr(load(), name)(grid.handle, _ptr(qx), _ptr(qy), m, int(k), _ptr(out_idx),
+                                 _ptr(out_dist), _ptr(out_robs), _stream(stream)), name)
     return out_idx, out_dist, out_robs
+
+
+def aidw_knn(grid: Grid, qx, qy, k: int, out_idx=None, out_dist=None, out_robs=None,
+             want=("idx", "dist", "robs"), stream=None):
+    """Grid kNN.  Allocates the outputs named in ``want`` that are not given.
+    Returns (idx int32 [m,k] | None, dist float32 [m,k] | None, robs float32 [m] | None)."""
+    return _knn_call("aidw_knn", grid, qx, qy, k, out_idx, out_dist, out_robs, want, stream)
 
 
 def aidw_knn_bruteforce(grid: Grid, qx, qy, k: int, out_idx=None, out_dist=None, out_robs=None,
                         want=("idx", "dist", "robs"), stream=None):
     """All-points per-thread kNN (the paper's original algorithm); same
     outputs as aidw_knn."""
-    import torch
-    qx, qy = _f32_dev(qx, "qx"), _f32_dev(qy, "qy")
-    m = qx.numel()
-    if out_idx is None and "idx" in want:
-        out_idx = torch.empty((m, k), dtype=torch.int32, device=qx.device)
-    if out_dist is None and "dist" in want:
-        out_dist = torch.empty((m, k), dtype=torch.float32, device=qx.device)
-    if out_robs is None and "robs" in want:
-        out_robs = torch.empty(m, dtype=torch.float32, device=qx.device)
-    _check(load().aidw_knn_bruteforce(grid.handle, _ptr(qx), _ptr(qy), m, int(k), _ptr(out_idx),
-                                      _ptr(out_dist), _ptr(out_robs), _stream(stream)),
-           "aidw_knn_bruteforce")
-    return out_idx, out_dist, out_robs
+    return _knn_call("aidw_knn_bruteforce", grid, qx, qy, k, out_idx, out_dist, out_robs, want,
+                     stream)
+
+
+def aidw_knn_paper_rule(grid: Grid, qx, qy, k: int, out_idx=None, out_dist=None, out_robs=None,
+                        want=("idx", "dist", "robs"), stream=None):
+    """Grid kNN with the paper's level rule (not always exact); same outputs
+    as aidw_knn."""
+    return _knn_call("aidw_knn_paper_rule", grid, qx, qy, k, out_idx, out_dist, out_robs, want,
+                     stream)
 
 
 def aidw_interpolate(grid: Grid, qx, qy, params: Params | None = None, out_z=None,

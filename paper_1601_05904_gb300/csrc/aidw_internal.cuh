@@ -113,8 +113,12 @@ struct KnnJob {
     long long nq;
     long long q_base;
     int k;
-    int pad_;
+    int stop_rule;  // kStopExact, or kStopPaperLevel (the paper's rule, Sec. 3.2.4)
 };
+
+// Stop rules of the ring search.
+constexpr int kStopExact = 0;       // stop once no unvisited cell can hold a nearer point
+constexpr int kStopPaperLevel = 1;  // first level whose block holds k points, plus one
 
 // One weighting job.  Units of all jobs are numbered job after job
 // (unit_base), and so are their query tiles (tile_base) and queries (q_base).
@@ -136,7 +140,8 @@ struct WJob {
 aidw_status knn_launch(const aidw_grid *g, const float *qx, const float *qy, long long n_query,
                        int k, bool fp64, const AlphaParams &ap, QRec *recs, int *out_idx,
                        float *out_dist, float *out_robs, void *out_alpha, cudaStream_t s,
-                       void *out_zlocal = nullptr, bool sort = true);
+                       void *out_zlocal = nullptr, bool sort = true,
+                       int stop_rule = kStopExact);
 
 // Brute-force kNN over all data points of the grid (the paper's original
 // per-thread algorithm, kept as a baseline).

@@ -430,6 +430,21 @@ aidw_status aidw_knn_bruteforce(const aidw_grid *g, const float *qx, const float
                             reinterpret_cast<cudaStream_t>(stream));
 }
 
+aidw_status aidw_knn_paper_rule(const aidw_grid *g, const float *qx, const float *qy,
+                                int64_t n_query, int k, int32_t *out_idx, float *out_dist,
+                                float *out_robs, aidw_stream_t stream)
+{
+    if (!g || n_query < 0 || n_query > kMaxPoints) return AIDW_ERR_INVALID_ARG;
+    if (k < 1 || k > AIDW_MAX_K || k > g->n_data) return AIDW_ERR_K_RANGE;
+    if (n_query == 0) return AIDW_OK;
+    if (!qx || !qy) return AIDW_ERR_INVALID_ARG;
+    aidw_params p;
+    aidw_params_default(&p);
+    return knn_launch(g, qx, qy, n_query, k, false, alpha_params(&p), nullptr, out_idx, out_dist,
+                      out_robs, nullptr, reinterpret_cast<cudaStream_t>(stream), nullptr, true,
+                      kStopPaperLevel);
+}
+
 aidw_status aidw_interpolate_local(const aidw_grid *g, const float *qx, const float *qy,
                                    int64_t n_query, const aidw_params *p, void *out_z,
                                    void *out_alpha, aidw_stream_t stream)

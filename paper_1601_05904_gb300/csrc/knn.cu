@@ -17,7 +17,9 @@
 // (the distance from the query to the block's nearest outer edge) is
 // farther than the current k-th distance, with a relative margin that covers
 // the rounding of the float32 distances and of the cell assignment.  Sides
-// of the block that reach the edge of the grid exclude nothing.
+// of the block that reach the edge of the grid exclude nothing.  The
+// paper's own rule is kept as an option (kStopPaperLevel, used by
+// aidw_knn_paper_rule) to measure how often it misses a neighbour.
 //
 // After the search the thread computes r_obs (Eq. 3), R (Eq. 4), mu (Eq. 5)
 // and alpha (Eq. 6) in float64 and writes one record for the weighting
@@ -152,6 +154,7 @@ __global__ void __launch_bounds__(kKnnMaxThreads)
     long long found = 0;
     int n_hit = 0;
     double hit_sum = 0.0;
+    int L0 = -1;  // paper rule: the first level whose block holds k points
 
     for (int L = 0;; ++L) {
         // Ring L as segments of one grid row each: the bottom and top edges
@@ -219,6 +222,11 @@ __global__ void __launch_bounds__(kKnnMaxThreads)
         const bool full_l = col - L <= 0, full_r = col + L >= nc - 1;
         const bool full_b = row - L <= 0, full_t = row + L >= nr - 1;
         if (full_l && full_r && full_b && full_t) break;  // whole grid visited
+        if (J.stop_rule == kStopPaperLevel) {
+            if (L0 < 0 && found >= k) L0 = L;
+            if (L0 >= 0 && L == L0 + 1) break;
+            continue;
+        }
         if (found >= k) {
             // distance from the query to the nearest edge of the block that
             // has cells beyond it
@@ -371,6 +379,7 @@ __global__ void __launch_bounds__(kKnnMaxThreads)
     long long found = 0;
     int n_hit = 0;
     double hit_sum = 0.0;
+    int L0 = -1;  // paper rule: the first level whose block holds k points
 
     for (int L = 0;; ++L) {
         const int c0 = max(col - L, 0), c1 = min(col + L, nc - 1);
@@ -434,6 +443,11 @@ __global__ void __launch_bounds__(kKnnMaxThreads)
         const bool full_l = col - L <= 0, full_r = col + L >= nc - 1;
         const bool full_b = row - L <= 0, full_t = row + L >= nr - 1;
         if (full_l && full_r && full_b && full_t) break;
+        if (J.stop_rule == kStopPaperLevel) {
+            if (L0 < 0 && found >= k) L0 = L;
+            if (L0 >= 0 && L == L0 + 1) break;
+            continue;
+        }
         if (found >= k) {
             double dmin = DistT<true>::inf();
             if (!full_l) dmin = fmin(dmin, (double)qx - (minx + (double)(col - L) * cw));
@@ -697,7 +711,7 @@ int knn_default_threads(int k)
 aidw_status knn_launch(const aidw_grid *g, const float *qx, const float *qy, long long n_query,
                        int k, bool fp64, const AlphaParams &ap, QRec *recs, int *out_idx,
                        float *out_dist, float *out_robs, void *out_alpha, cudaStream_t s,
-                       void *out_zlocal, bool sort)
+                       void *out_zlocal, bool sort, int stop_rule)
 {
     if (n_query <= 0) return AIDW_OK;
     KnnJob j;
@@ -717,7 +731,7 @@ aidw_status knn_launch(const aidw_grid *g, const float *qx, const float *qy, lon
     j.nq = n_query;
     j.q_base = 0;
     j.k = k;
-    j.pad_ = 0;
+    j.stop_rule = stop_rule;
     const int threads = out_zlocal ? kKnnThreads : knn_default_threads(k);
     const int prof = profile_begin(s);
     int launches = 1;

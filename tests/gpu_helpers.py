@@ -23,24 +23,29 @@ def host(t):
     return t.detach().cpu().numpy()
 
 
-def check_knn(oracle, x, y, qx, qy, k, idx_gpu, dist_gpu, robs_gpu=None):
-    """Compares a GPU kNN result with the oracle's brute force.
+def check_knn(oracle, x, y, qx, qy, k, idx_gpu, dist_gpu, robs_gpu=None, ref=None):
+    """Compares a GPU kNN result with the oracle's brute force (or with
+    ``ref`` = (idx, dist) of k or k+1 columns from another oracle search).
 
     Unique parts are compared exactly or to rounding: the sorted k smallest
     distances and, away from near-ties, the index set.  Where the oracle's
     k-th and (k+1)-th distances nearly tie, the GPU set may differ, and each
     GPU index must then be a point at the reported distance."""
     n = len(x)
-    kk = min(k + 1, n)
-    ridx, rd = oracle.knn(x, y, qx, qy, kk)
+    if ref is None:
+        ridx, rd = oracle.knn(x, y, qx, qy, min(k + 1, n))
+    else:
+        ridx, rd = ref
+    kk = rd.shape[1]
     d_ref = rd[:, :k]
     np.testing.assert_allclose(dist_gpu.astype(np.float64), d_ref, rtol=TOL_DIST, atol=1e-30)
     if robs_gpu is not None:
         np.testing.assert_allclose(robs_gpu.astype(np.float64), d_ref.mean(1), rtol=2 * TOL_DIST)
     same = np.array([set(a) == set(b) for a, b in zip(idx_gpu.tolist(), ridx[:, :k].tolist())])
     if kk > k:
-        gap = (rd[:, k] - rd[:, k - 1]) / np.maximum(rd[:, k], 1e-300)
-        near = gap < NEAR_TIE
+        with np.errstate(invalid="ignore"):
+            gap = (rd[:, k] - rd[:, k - 1]) / np.maximum(rd[:, k], 1e-300)
+        near = np.isfinite(rd[:, k]) & (gap < NEAR_TIE)
     else:
         near = np.zeros(len(qx), bool)
     bad = ~same & ~near
