@@ -1,9 +1,11 @@
 """Shared helpers for the GPU parity tests (no method arithmetic here)."""
 import numpy as np
 
-# Tolerances (see the readings of the method in the design doc):
+# Tolerances:
 #  - float32-compensated predictions: max |z - z_ref| / S_q <= 1e-5, S_q =
-#    sum w|z| / sum w from the oracle;
+#    sum w|z| / sum w from the oracle (a relative error is ill-posed where
+#    the signed field makes sum w z cancel, so the error is scaled by the
+#    magnitude of the terms that are summed);
 #  - float64 predictions: the same measure <= 1e-9;
 #  - kNN distances: float32 rounding of float32 coordinates, <= 1e-6 relative;
 #  - kNN index sets: exact unless the oracle's k-th and (k+1)-th distances are
