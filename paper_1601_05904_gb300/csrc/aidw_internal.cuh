@@ -93,6 +93,8 @@ struct AlphaParams {
     double level[5];
     double r_min, r_max;
     double area_override;  // > 0 replaces the grid's area in Eq. 2
+    // float32 copies for the float32 path's Eq. 4-5 (pi / R_max as printed)
+    float r_min_f, r_max_f, pi_over_rmax_f, area_override_f;
 };
 
 // One kNN job: a grid, its queries and where the results go.  Batched

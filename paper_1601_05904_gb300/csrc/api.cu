@@ -211,6 +211,10 @@ AlphaParams alpha_params(const aidw_params *p)
     ap.r_min = p->r_min;
     ap.r_max = p->r_max;
     ap.area_override = p->area > 0.0 ? p->area : 0.0;
+    ap.r_min_f = (float)p->r_min;
+    ap.r_max_f = (float)p->r_max;
+    ap.pi_over_rmax_f = (float)(3.141592653589793 / p->r_max);
+    ap.area_override_f = (float)ap.area_override;
     return ap;
 }
 

@@ -78,6 +78,78 @@ __device__ __forceinline__ int knn_job_of(const KnnJob *__restrict__ jobs, int n
     return lo;
 }
 
+// Stop-rule bounds.  The distance from the query to the outer edge of the
+// level-L block on one side is its distance to that edge of its own cell
+// plus L cell widths.  The four own-cell distances are taken once in
+// float64, less a bound on the float64 rounding of the edge positions and
+// of the points' cell assignment, and kept as float32 values rounded down;
+// each ring then steps them with round-down float32 arithmetic.  Every value
+// is a lower bound of the true edge distance, so the stop test can only be
+// late, never early, and no ring costs float64 work.
+struct EdgeBounds {
+    float l, r, b, t, cw;
+};
+
+__device__ __forceinline__ EdgeBounds edge_bounds(float qx, float qy, const GridDev *g, int col,
+                                                  int row)
+{
+    const double minx = g->min_x, miny = g->min_y, cw = g->cw;
+    const double margin = 4.0e-16 * (fabs((double)qx) + fabs((double)qy) + fabs(minx) +
+                                      fabs(miny) + (double)(g->n_col + g->n_row + 2) * cw);
+    EdgeBounds e;
+    e.l = __double2float_rd((double)qx - (minx + (double)col * cw) - margin);
+    e.r = __double2float_rd((minx + (double)(col + 1) * cw) - (double)qx - margin);
+    e.b = __double2float_rd((double)qy - (miny + (double)row * cw) - margin);
+    e.t = __double2float_rd((miny + (double)(row + 1) * cw) - (double)qy - margin);
+    e.cw = __double2float_rd(cw);
+    return e;
+}
+
+// True when no point outside the level-L block (sides that reach the grid's
+// edge exclude nothing) can come before the current k-th entry: the block's
+// nearest open edge, squared and shrunk by a relative 2^-20 that covers the
+// rounding of the float32 squared distances, is beyond the k-th distance.
+template <typename D>
+__device__ __forceinline__ bool block_is_final(const EdgeBounds &e, float Lf, bool full_l,
+                                               bool full_r, bool full_b, bool full_t, D kth)
+{
+    const float inf = __int_as_float(0x7f800000);
+    const float step = __fmul_rd(Lf, e.cw);
+    float dmin = inf;
+    if (!full_l) dmin = fminf(dmin, __fadd_rd(e.l, step));
+    if (!full_r) dmin = fminf(dmin, __fadd_rd(e.r, step));
+    if (!full_b) dmin = fminf(dmin, __fadd_rd(e.b, step));
+    if (!full_t) dmin = fminf(dmin, __fadd_rd(e.t, step));
+    return dmin > 0.0f && (D)__fmul_rd(__fmul_rd(dmin, dmin), 0.99999904632568359375f) > kth;
+}
+
+// Eq. 3-5 for the float32 path, whose weights take alpha rounded to float32:
+// r_obs from correctly rounded float32 square roots summed in float64, R and
+// the Eq. 5 cosine in float32 (a few float32 ulps of alpha; the float64 path
+// evaluates Eq. 3-5 in float64).  Edge cases as nn_statistic / membership.
+template <int KMAX, typename D>
+__device__ __forceinline__ float robs_f32(const D (&kd)[KMAX], int k)
+{
+    double rs = 0.0;
+#pragma unroll
+    for (int j = 0; j < KMAX; ++j)
+        if (j < k) rs += (double)sqrtf((float)kd[j]);
+    return (float)rs / (float)k;
+}
+
+__device__ __forceinline__ double membership_f32(float r_obs, const GridDev *g,
+                                                 const AlphaParams &ap)
+{
+    const float r_exp = ap.area_override_f > 0.0f
+                            ? 0.5f / sqrtf((float)g->n_data / ap.area_override_f)
+                            : (float)g->r_exp;
+    const float R = r_obs == 0.0f ? 0.0f
+                                  : (r_exp == 0.0f ? __int_as_float(0x7f800000) : r_obs / r_exp);
+    if (R <= ap.r_min_f) return 0.0;
+    if (R >= ap.r_max_f) return 1.0;
+    return 0.5 - 0.5 * (double)cosf(ap.pi_over_rmax_f * (R - ap.r_min_f));
+}
+
 template <bool F64, int KMAX>
 __global__ void __launch_bounds__(kKnnMaxThreads)
     k_knn(KnnJob job0, const KnnJob *__restrict__ jobs, int n_jobs, long long total_q,
@@ -141,6 +213,7 @@ __global__ void __launch_bounds__(kKnnMaxThreads)
     long long roww = (long long)floor(((double)qy - miny) / cw);
     const int col = (int)(colw < 0 ? 0 : (colw > nc - 1 ? nc - 1 : colw));
     const int row = (int)(roww < 0 ? 0 : (roww > nr - 1 ? nr - 1 : roww));
+    const EdgeBounds eb = edge_bounds(qx, qy, g, col, row);
 
     D kd[KMAX];
     int ki[KMAX];
@@ -227,33 +300,27 @@ __global__ void __launch_bounds__(kKnnMaxThreads)
             if (L0 >= 0 && L == L0 + 1) break;
             continue;
         }
-        if (found >= k) {
-            // distance from the query to the nearest edge of the block that
-            // has cells beyond it
-            double dmin = DistT<true>::inf();
-            if (!full_l) dmin = fmin(dmin, (double)qx - (minx + (double)(col - L) * cw));
-            if (!full_r) dmin = fmin(dmin, (minx + (double)(col + L + 1) * cw) - (double)qx);
-            if (!full_b) dmin = fmin(dmin, (double)qy - (miny + (double)(row - L) * cw));
-            if (!full_t) dmin = fmin(dmin, (miny + (double)(row + L + 1) * cw) - (double)qy);
-            // margin for the float64 edge positions (absolute) and the
-            // float32 distance rounding (relative)
-            dmin -= 4.0e-16 * (fabs((double)qx) + fabs((double)qy) + fabs(minx) + fabs(miny) +
-                               (double)(nc + nr + 2) * cw);
-            if (dmin > 0.0 && dmin * dmin * (1.0 - 0x1p-20) > (double)kth) break;
-        }
+        if (found >= k && block_is_final(eb, (float)L, full_l, full_r, full_b, full_t, kth))
+            break;
     }
 
     // Eq. 3 (r_obs), Eq. 2 (r_exp, possibly with an explicit area), Eq. 4-6.
-    double r_obs = 0.0;
+    double r_obs, mu;
+    if (F64) {
+        r_obs = 0.0;
 #pragma unroll
-    for (int j = 0; j < KMAX; ++j)
-        if (j < k) r_obs += sqrt((double)kd[j]);
-    r_obs /= (double)k;
-    const double r_exp = ap.area_override > 0.0
-                             ? 1.0 / (2.0 * sqrt((double)g->n_data / ap.area_override))
-                             : g->r_exp;
-    const double R = nn_statistic(r_obs, r_exp);
-    const double mu = membership(R, ap.r_min, ap.r_max);
+        for (int j = 0; j < KMAX; ++j)
+            if (j < k) r_obs += sqrt((double)kd[j]);
+        r_obs /= (double)k;
+        const double r_exp = ap.area_override > 0.0
+                                 ? 1.0 / (2.0 * sqrt((double)g->n_data / ap.area_override))
+                                 : g->r_exp;
+        mu = membership(nn_statistic(r_obs, r_exp), ap.r_min, ap.r_max);
+    } else {
+        const float rf = robs_f32<KMAX>(kd, k);
+        r_obs = rf;
+        mu = membership_f32(rf, g, ap);
+    }
     const double alpha =
         decay_power(mu, ap.level[0], ap.level[1], ap.level[2], ap.level[3], ap.level[4]);
 
@@ -371,6 +438,7 @@ __global__ void __launch_bounds__(kKnnMaxThreads)
     long long roww = (long long)floor(((double)qy - miny) / cw);
     const int col = (int)(colw < 0 ? 0 : (colw > nc - 1 ? nc - 1 : colw));
     const int row = (int)(roww < 0 ? 0 : (roww > nr - 1 ? nr - 1 : roww));
+    const EdgeBounds eb = edge_bounds(qx, qy, g, col, row);
 
     D md = DistT<F64>::inf();  // this lane's entry of the sorted top-k list
     int mi = 0x7fffffff;
@@ -448,31 +516,29 @@ __global__ void __launch_bounds__(kKnnMaxThreads)
             if (L0 >= 0 && L == L0 + 1) break;
             continue;
         }
-        if (found >= k) {
-            double dmin = DistT<true>::inf();
-            if (!full_l) dmin = fmin(dmin, (double)qx - (minx + (double)(col - L) * cw));
-            if (!full_r) dmin = fmin(dmin, (minx + (double)(col + L + 1) * cw) - (double)qx);
-            if (!full_b) dmin = fmin(dmin, (double)qy - (miny + (double)(row - L) * cw));
-            if (!full_t) dmin = fmin(dmin, (miny + (double)(row + L + 1) * cw) - (double)qy);
-            dmin -= 4.0e-16 * (fabs((double)qx) + fabs((double)qy) + fabs(minx) + fabs(miny) +
-                               (double)(nc + nr + 2) * cw);
-            if (dmin > 0.0 && dmin * dmin * (1.0 - 0x1p-20) > (double)kth) break;
-        }
+        if (found >= k && block_is_final(eb, (float)L, full_l, full_r, full_b, full_t, kth))
+            break;
     }
 
     // Eq. 3-6 (the order of the r_obs sum differs from k_knn only in rounding)
-    double rs = lane < k ? sqrt((double)md) : 0.0;
+    double rs = lane < k ? (F64 ? sqrt((double)md) : (double)sqrtf((float)md)) : 0.0;
     for (int o = 16; o > 0; o >>= 1) {
         rs += __shfl_xor_sync(full, rs, o);
         n_hit += __shfl_xor_sync(full, n_hit, o);
         hit_sum += __shfl_xor_sync(full, hit_sum, o);
     }
-    const double r_obs = rs / (double)k;
-    const double r_exp = ap.area_override > 0.0
-                             ? 1.0 / (2.0 * sqrt((double)g->n_data / ap.area_override))
-                             : g->r_exp;
-    const double R = nn_statistic(r_obs, r_exp);
-    const double mu = membership(R, ap.r_min, ap.r_max);
+    double r_obs, mu;
+    if (F64) {
+        r_obs = rs / (double)k;
+        const double r_exp = ap.area_override > 0.0
+                                 ? 1.0 / (2.0 * sqrt((double)g->n_data / ap.area_override))
+                                 : g->r_exp;
+        mu = membership(nn_statistic(r_obs, r_exp), ap.r_min, ap.r_max);
+    } else {
+        const float rf = (float)rs / (float)k;
+        r_obs = rf;
+        mu = membership_f32(rf, g, ap);
+    }
     const double alpha =
         decay_power(mu, ap.level[0], ap.level[1], ap.level[2], ap.level[3], ap.level[4]);
     const D d1 = __shfl_sync(full, md, 0);
@@ -564,16 +630,14 @@ __global__ void __launch_bounds__(kBruteThreads)
         }
     }
     if (!active) return;
-    double r_obs = 0.0;
 #pragma unroll
     for (int j = 0; j < KMAX; ++j) {
         if (j < k) {
-            r_obs += sqrt((double)kd[j]);
             if (out_idx) out_idx[q * k + j] = ki[j];
             if (out_dist) out_dist[q * k + j] = sqrtf(kd[j]);
         }
     }
-    if (out_robs) out_robs[q] = (float)(r_obs / (double)k);
+    if (out_robs) out_robs[q] = robs_f32<KMAX>(kd, k);  // as the grid kNN's float32 path
 }
 
 template <bool F64, int KMAX>
