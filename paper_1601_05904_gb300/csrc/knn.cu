@@ -128,12 +128,12 @@ __device__ __forceinline__ bool block_is_final(const EdgeBounds &e, float Lf, bo
 // the Eq. 5 cosine in float32 (a few float32 ulps of alpha; the float64 path
 // evaluates Eq. 3-5 in float64).  Edge cases as nn_statistic / membership.
 template <int KMAX, typename D>
-__device__ __forceinline__ float robs_f32(const D (&kd)[KMAX], int k)
+__device__ __forceinline__ float robs_f32(const D (&kd)[KMAX], int lo, int k)
 {
-    double rs = 0.0;
+    double rs = 0.0;  // entries kd[lo .. lo + k), ascending
 #pragma unroll
     for (int j = 0; j < KMAX; ++j)
-        if (j < k) rs += (double)sqrtf((float)kd[j]);
+        if (j >= lo && j < lo + k) rs += (double)sqrtf((float)kd[j]);
     return (float)rs / (float)k;
 }
 
@@ -215,12 +215,16 @@ __global__ void __launch_bounds__(kKnnMaxThreads)
     const int row = (int)(roww < 0 ? 0 : (roww > nr - 1 ? nr - 1 : roww));
     const EdgeBounds eb = edge_bounds(qx, qy, g, col, row);
 
+    // The k best (d^2, index) pairs, ascending, in the top k slots
+    // [lo, KMAX): the k-th is always kd[KMAX - 1].  The slots below lo hold
+    // -inf sentinels, which stop a candidate that bubbles down from the top.
+    const int lo = KMAX - k;
     D kd[KMAX];
     int ki[KMAX];
 #pragma unroll
     for (int j = 0; j < KMAX; ++j) {
-        kd[j] = DistT<F64>::inf();
-        ki[j] = 0x7fffffff;
+        kd[j] = j < lo ? -DistT<F64>::inf() : DistT<F64>::inf();
+        ki[j] = j < lo ? -1 : 0x7fffffff;
     }
     D kth = DistT<F64>::inf();
     int kthi = 0x7fffffff;
@@ -267,28 +271,26 @@ __global__ void __launch_bounds__(kKnnMaxThreads)
                     hit_sum += (double)p.z;
                 }
                 if (d2 < kth || (d2 == kth && pidx < kthi)) {
-                    // bubble the candidate through the sorted list
-                    D cd = d2;
-                    int ci = pidx;
+                    // replace the k-th and bubble the candidate down to its
+                    // place: with an early exit for short lists, as one
+                    // branch-free pass for 32 slots (an exit chain that long
+                    // costs registers and diverges; measured 2x slower)
+                    kd[KMAX - 1] = d2;
+                    ki[KMAX - 1] = pidx;
 #pragma unroll
-                    for (int j = 0; j < KMAX; ++j) {
-                        const bool lt = (j < k) && (cd < kd[j] || (cd == kd[j] && ci < ki[j]));
-                        const D td = kd[j];
-                        const int ti = ki[j];
-                        kd[j] = lt ? cd : td;
-                        ki[j] = lt ? ci : ti;
-                        cd = lt ? td : cd;
-                        ci = lt ? ti : ci;
+                    for (int j = KMAX - 1; j > 0; --j) {
+                        const bool sw =
+                            kd[j] < kd[j - 1] || (kd[j] == kd[j - 1] && ki[j] < ki[j - 1]);
+                        if (KMAX <= 16 && !sw) break;
+                        const D td = kd[j], tl = kd[j - 1];
+                        const int ti = ki[j], tj = ki[j - 1];
+                        kd[j] = sw ? tl : td;
+                        ki[j] = sw ? tj : ti;
+                        kd[j - 1] = sw ? td : tl;
+                        ki[j - 1] = sw ? ti : tj;
                     }
-                    kth = kd[0];
-                    kthi = ki[0];
-#pragma unroll
-                    for (int j = 1; j < KMAX; ++j) {
-                        if (j == k - 1) {
-                            kth = kd[j];
-                            kthi = ki[j];
-                        }
-                    }
+                    kth = kd[KMAX - 1];
+                    kthi = ki[KMAX - 1];
                 }
             }
         }
@@ -310,34 +312,38 @@ __global__ void __launch_bounds__(kKnnMaxThreads)
         r_obs = 0.0;
 #pragma unroll
         for (int j = 0; j < KMAX; ++j)
-            if (j < k) r_obs += sqrt((double)kd[j]);
+            if (j >= lo) r_obs += sqrt((double)kd[j]);
         r_obs /= (double)k;
         const double r_exp = ap.area_override > 0.0
                                  ? 1.0 / (2.0 * sqrt((double)g->n_data / ap.area_override))
                                  : g->r_exp;
         mu = membership(nn_statistic(r_obs, r_exp), ap.r_min, ap.r_max);
     } else {
-        const float rf = robs_f32<KMAX>(kd, k);
+        const float rf = robs_f32<KMAX>(kd, lo, k);
         r_obs = rf;
         mu = membership_f32(rf, g, ap);
     }
     const double alpha =
         decay_power(mu, ap.level[0], ap.level[1], ap.level[2], ap.level[3], ap.level[4]);
 
+    D d1 = kd[KMAX - 1];  // the nearest, kd[lo]
+#pragma unroll
+    for (int j = 0; j < KMAX - 1; ++j)
+        if (j == lo) d1 = kd[j];
     if (recs) {
         QRec r;
         r.alpha = alpha;
         r.hit_z = n_hit > 0 ? hit_sum / (double)n_hit : 0.0;
-        r.d1sq = (float)kd[0];
+        r.d1sq = (float)d1;
         r.n_hit = n_hit;
         recs[q] = r;
     }
     if (out_idx || out_dist) {
 #pragma unroll
         for (int j = 0; j < KMAX; ++j) {
-            if (j < k) {
-                if (out_idx) out_idx[q * k + j] = ki[j];
-                if (out_dist) out_dist[q * k + j] = (float)sqrt(kd[j]);
+            if (j >= lo) {
+                if (out_idx) out_idx[q * k + j - lo] = ki[j];
+                if (out_dist) out_dist[q * k + j - lo] = (float)sqrt(kd[j]);
             }
         }
     }
@@ -353,12 +359,12 @@ __global__ void __launch_bounds__(kKnnMaxThreads)
         // path, SFU, largest weight 1) or pow(d^2, -alpha/2) (float64 path),
         // sums in float64; coincident neighbours give their mean z.
         const float c = (float)(-0.5 * alpha);
-        const float b = F64 ? 0.0f : -c * lg2_sfu((float)kd[0]);
+        const float b = F64 ? 0.0f : -c * lg2_sfu((float)d1);
         double sw = 0.0, swz = 0.0, hz = 0.0;
         int nh = 0;
 #pragma unroll
         for (int j = 0; j < KMAX; ++j) {
-            if (j < k) {
+            if (j >= lo) {
                 const double zj = (double)J.zorig[ki[j]];
                 if (kd[j] == (D)0) {
                     ++nh;
@@ -637,7 +643,7 @@ __global__ void __launch_bounds__(kBruteThreads)
             if (out_dist) out_dist[q * k + j] = sqrtf(kd[j]);
         }
     }
-    if (out_robs) out_robs[q] = robs_f32<KMAX>(kd, k);  // as the grid kNN's float32 path
+    if (out_robs) out_robs[q] = robs_f32<KMAX>(kd, 0, k);  // as the grid kNN's float32 path
 }
 
 template <bool F64, int KMAX>
