@@ -20,6 +20,10 @@ struct GridDev {
     double r_exp;       // Eq. 2
     double cw;          // cell width
     long long n_col, n_row, n_cells;
+    // float32 forms for the cell-index fast path and the stop-test bounds:
+    // min_x/min_y exactly (they are float32 values), 1/cw rounded to
+    // nearest, cw rounded down and up
+    float min_x_f, min_y_f, inv_cw_f, cw_rd, cw_ru, pad_f;
     long long n_data;
     int status;         // latched AIDW error bits (see StatusBit)
     int pad_;
@@ -93,7 +97,8 @@ struct AlphaParams {
     double level[5];
     double r_min, r_max;
     double area_override;  // > 0 replaces the grid's area in Eq. 2
-    // float32 copies for the float32 path's Eq. 4-5 (pi / R_max as printed)
+    // float32 copies for the float32 path's Eq. 4-6 (pi / R_max as printed)
+    float level_f[5];
     float r_min_f, r_max_f, pi_over_rmax_f, area_override_f;
 };
 

@@ -211,6 +211,7 @@ AlphaParams alpha_params(const aidw_params *p)
     ap.r_min = p->r_min;
     ap.r_max = p->r_max;
     ap.area_override = p->area > 0.0 ? p->area : 0.0;
+    for (int i = 0; i < 5; ++i) ap.level_f[i] = (float)p->alpha[i];
     ap.r_min_f = (float)p->r_min;
     ap.r_max_f = (float)p->r_max;
     ap.pi_over_rmax_f = (float)(3.141592653589793 / p->r_max);

@@ -105,6 +105,8 @@ __device__ __forceinline__ void grid_dims(GridDev *g, double cell_scale, double 
         g->area = 0.0;
         g->r_exp = 0.0;
         g->cw = 1.0;
+        g->min_x_f = g->min_y_f = 0.0f;
+        g->inv_cw_f = g->cw_rd = g->cw_ru = 1.0f;
         g->n_col = g->n_row = g->n_cells = 1;
         return;
     }
@@ -131,6 +133,11 @@ __device__ __forceinline__ void grid_dims(GridDev *g, double cell_scale, double 
     g->area = area;
     g->r_exp = r_exp;
     g->cw = cw;
+    g->min_x_f = (float)minx;
+    g->min_y_f = (float)miny;
+    g->inv_cw_f = (float)(1.0 / cw);
+    g->cw_rd = __double2float_rd(cw);
+    g->cw_ru = __double2float_ru(cw);
     g->n_col = (long long)((W + cw) / cw);
     g->n_row = (long long)((H + cw) / cw);
     g->n_cells = g->n_col * g->n_row;
@@ -142,16 +149,37 @@ __device__ __forceinline__ bool grid_failed(const GridDev *g)
     return (g->status & (kStatusNonfiniteData | kStatusCapacity)) != 0;
 }
 
+// floor((x - min) / cw) of the cell formula, equal to the floor of the
+// correctly rounded float64 quotient of the float64 difference (the
+// definition).  Fast path in float32: x and min are float32 values, and
+// q = fl32(fl32(x - min) * fl32(1/cw)) is within 3 * 2^-24 (+ tiny) of the
+// exact quotient, relatively, as is the float64 quotient; so where q is
+// farther than 2^-21 |q| from every integer the two have the same floor
+// (q - floor(q) and floor(q) + 1 - q are exact for |q| < 2^23; beyond that
+// the margin exceeds 1 and the test always fails).  Otherwise - about one
+// coordinate in 10^3 at a thousand cells per side - the float64 division
+// is used.  Float64 runs at a small fraction of float32 on this GPU.
+// Negative and huge quotients (queries outside the grid) are clamped by
+// the caller, so an inexact floor there changes nothing.
+__device__ __forceinline__ long long cell_floor(float x, float min_f, float inv_f, double min_d,
+                                                double cw)
+{
+    const float q = __fmul_rn(__fsub_rn(x, min_f), inv_f);
+    const float f = floorf(q);
+    const float tol = fabsf(q) * 0x1p-21f;
+    if (q - f > tol && (f + 1.0f) - q > tol) return (long long)f;
+    return (long long)floor(((double)x - min_d) / cw);
+}
+
 // Cell of the point (x, y) stored as item i, and its (unstable) rank among
 // the items of that cell.
 __device__ __forceinline__ void key_one_xy(long long i, float x, float y, const GridDev *g,
                                            int *__restrict__ count, int *__restrict__ key,
                                            int *__restrict__ rank)
 {
-    const double minx = g->min_x, miny = g->min_y, cw = g->cw;
     const long long nc = g->n_col, nr = g->n_row;
-    long long col = (long long)floor(((double)x - minx) / cw);
-    long long row = (long long)floor(((double)y - miny) / cw);
+    long long col = cell_floor(x, g->min_x_f, g->inv_cw_f, g->min_x, g->cw);
+    long long row = cell_floor(y, g->min_y_f, g->inv_cw_f, g->min_y, g->cw);
     col = col < 0 ? 0 : (col > nc - 1 ? nc - 1 : col);
     row = row < 0 ? 0 : (row > nr - 1 ? nr - 1 : row);
     const int c = (int)(row * nc + col);

@@ -80,12 +80,13 @@ __device__ __forceinline__ int knn_job_of(const KnnJob *__restrict__ jobs, int n
 
 // Stop-rule bounds.  The distance from the query to the outer edge of the
 // level-L block on one side is its distance to that edge of its own cell
-// plus L cell widths.  The four own-cell distances are taken once in
-// float64, less a bound on the float64 rounding of the edge positions and
-// of the points' cell assignment, and kept as float32 values rounded down;
-// each ring then steps them with round-down float32 arithmetic.  Every value
-// is a lower bound of the true edge distance, so the stop test can only be
-// late, never early, and no ring costs float64 work.
+// plus L cell widths.  The four own-cell distances are lower bounds taken
+// once per query in float32 with directed rounding (edge positions rounded
+// away from the query, cw rounded down), less a margin for the float64
+// rounding of the points' cell assignment (a point of column c lies at
+// least c * cw * 2^-52 short of its cell's edge); each ring then steps them
+// with round-down arithmetic.  Every value is a lower bound of the true
+// edge distance, so the stop test can only be late, never early.
 struct EdgeBounds {
     float l, r, b, t, cw;
 };
@@ -93,15 +94,16 @@ struct EdgeBounds {
 __device__ __forceinline__ EdgeBounds edge_bounds(float qx, float qy, const GridDev *g, int col,
                                                   int row)
 {
-    const double minx = g->min_x, miny = g->min_y, cw = g->cw;
-    const double margin = 4.0e-16 * (fabs((double)qx) + fabs((double)qy) + fabs(minx) +
-                                      fabs(miny) + (double)(g->n_col + g->n_row + 2) * cw);
+    // (at least the smallest normal float32: results flushed to zero are off
+    // by less than that)
+    const float margin = fmaxf(
+        __fmul_ru(__fmul_ru((float)(g->n_col + g->n_row + 2), g->cw_ru), 0x1p-50f), 0x1p-126f);
     EdgeBounds e;
-    e.l = __double2float_rd((double)qx - (minx + (double)col * cw) - margin);
-    e.r = __double2float_rd((minx + (double)(col + 1) * cw) - (double)qx - margin);
-    e.b = __double2float_rd((double)qy - (miny + (double)row * cw) - margin);
-    e.t = __double2float_rd((miny + (double)(row + 1) * cw) - (double)qy - margin);
-    e.cw = __double2float_rd(cw);
+    e.l = __fsub_rd(__fsub_rd(qx, __fmaf_ru((float)col, g->cw_ru, g->min_x_f)), margin);
+    e.r = __fsub_rd(__fsub_rd(__fmaf_rd((float)(col + 1), g->cw_rd, g->min_x_f), qx), margin);
+    e.b = __fsub_rd(__fsub_rd(qy, __fmaf_ru((float)row, g->cw_ru, g->min_y_f)), margin);
+    e.t = __fsub_rd(__fsub_rd(__fmaf_rd((float)(row + 1), g->cw_rd, g->min_y_f), qy), margin);
+    e.cw = g->cw_rd;
     return e;
 }
 
@@ -123,31 +125,43 @@ __device__ __forceinline__ bool block_is_final(const EdgeBounds &e, float Lf, bo
     return dmin > 0.0f && (D)__fmul_rd(__fmul_rd(dmin, dmin), 0.99999904632568359375f) > kth;
 }
 
-// Eq. 3-5 for the float32 path, whose weights take alpha rounded to float32:
-// r_obs from correctly rounded float32 square roots summed in float64, R and
-// the Eq. 5 cosine in float32 (a few float32 ulps of alpha; the float64 path
-// evaluates Eq. 3-5 in float64).  Edge cases as nn_statistic / membership.
+// Eq. 3-6 for the float32 path, whose weights take alpha rounded to
+// float32: r_obs as a TwoSum-compensated float32 sum of correctly rounded
+// float32 square roots, R, the Eq. 5 cosine and Eq. 6 in float32 (alpha
+// within a few float32 ulps; the float64 path evaluates Eq. 3-6 in float64,
+// which on this GPU costs as much as the whole ring search).  Edge cases as
+// nn_statistic / membership / decay_power.
 template <int KMAX, typename D>
 __device__ __forceinline__ float robs_f32(const D (&kd)[KMAX], int lo, int k)
 {
-    double rs = 0.0;  // entries kd[lo .. lo + k), ascending
+    float hi = 0.0f, err = 0.0f;  // entries kd[lo .. lo + k), ascending
 #pragma unroll
     for (int j = 0; j < KMAX; ++j)
-        if (j >= lo && j < lo + k) rs += (double)sqrtf((float)kd[j]);
-    return (float)rs / (float)k;
+        if (j >= lo && j < lo + k) comp_add(hi, err, sqrtf((float)kd[j]));
+    return __fdiv_rn(add_rn(hi, err), (float)k);
 }
 
-__device__ __forceinline__ double membership_f32(float r_obs, const GridDev *g,
-                                                 const AlphaParams &ap)
+__device__ __forceinline__ float membership_f32(float r_obs, const GridDev *g,
+                                                const AlphaParams &ap)
 {
     const float r_exp = ap.area_override_f > 0.0f
                             ? 0.5f / sqrtf((float)g->n_data / ap.area_override_f)
                             : (float)g->r_exp;
     const float R = r_obs == 0.0f ? 0.0f
                                   : (r_exp == 0.0f ? __int_as_float(0x7f800000) : r_obs / r_exp);
-    if (R <= ap.r_min_f) return 0.0;
-    if (R >= ap.r_max_f) return 1.0;
-    return 0.5 - 0.5 * (double)cosf(ap.pi_over_rmax_f * (R - ap.r_min_f));
+    if (R <= ap.r_min_f) return 0.0f;
+    if (R >= ap.r_max_f) return 1.0f;
+    return 0.5f - 0.5f * cosf(ap.pi_over_rmax_f * (R - ap.r_min_f));
+}
+
+__device__ __forceinline__ float decay_power_f32(float mu, const float (&a)[5])
+{
+    if (mu <= 0.1f) return a[0];
+    if (mu <= 0.3f) return a[0] * (1.0f - 5.0f * (mu - 0.1f)) + 5.0f * a[1] * (mu - 0.1f);
+    if (mu <= 0.5f) return 5.0f * a[2] * (mu - 0.3f) + a[1] * (1.0f - 5.0f * (mu - 0.3f));
+    if (mu <= 0.7f) return a[2] * (1.0f - 5.0f * (mu - 0.5f)) + 5.0f * a[3] * (mu - 0.5f);
+    if (mu <= 0.9f) return 5.0f * a[4] * (mu - 0.7f) + a[3] * (1.0f - 5.0f * (mu - 0.7f));
+    return a[4];
 }
 
 template <bool F64, int KMAX>
@@ -209,8 +223,8 @@ __global__ void __launch_bounds__(kKnnMaxThreads)
 
     const double minx = g->min_x, miny = g->min_y, cw = g->cw;
     const int nc = (int)g->n_col, nr = (int)g->n_row;
-    long long colw = (long long)floor(((double)qx - minx) / cw);
-    long long roww = (long long)floor(((double)qy - miny) / cw);
+    long long colw = gridk::cell_floor(qx, g->min_x_f, g->inv_cw_f, minx, cw);
+    long long roww = gridk::cell_floor(qy, g->min_y_f, g->inv_cw_f, miny, cw);
     const int col = (int)(colw < 0 ? 0 : (colw > nc - 1 ? nc - 1 : colw));
     const int row = (int)(roww < 0 ? 0 : (roww > nr - 1 ? nr - 1 : roww));
     const EdgeBounds eb = edge_bounds(qx, qy, g, col, row);
@@ -307,7 +321,7 @@ __global__ void __launch_bounds__(kKnnMaxThreads)
     }
 
     // Eq. 3 (r_obs), Eq. 2 (r_exp, possibly with an explicit area), Eq. 4-6.
-    double r_obs, mu;
+    double r_obs, alpha;
     if (F64) {
         r_obs = 0.0;
 #pragma unroll
@@ -317,14 +331,15 @@ __global__ void __launch_bounds__(kKnnMaxThreads)
         const double r_exp = ap.area_override > 0.0
                                  ? 1.0 / (2.0 * sqrt((double)g->n_data / ap.area_override))
                                  : g->r_exp;
-        mu = membership(nn_statistic(r_obs, r_exp), ap.r_min, ap.r_max);
+        const double mu = membership(nn_statistic(r_obs, r_exp), ap.r_min, ap.r_max);
+        alpha = decay_power(mu, ap.level[0], ap.level[1], ap.level[2], ap.level[3], ap.level[4]);
     } else {
         const float rf = robs_f32<KMAX>(kd, lo, k);
         r_obs = rf;
-        mu = membership_f32(rf, g, ap);
+        alpha = decay_power_f32(membership_f32(rf, g, ap), ap.level_f);
     }
-    const double alpha =
-        decay_power(mu, ap.level[0], ap.level[1], ap.level[2], ap.level[3], ap.level[4]);
+    double hit_z = 0.0;
+    if (n_hit > 0) hit_z = hit_sum / (double)n_hit;
 
     D d1 = kd[KMAX - 1];  // the nearest, kd[lo]
 #pragma unroll
@@ -333,7 +348,7 @@ __global__ void __launch_bounds__(kKnnMaxThreads)
     if (recs) {
         QRec r;
         r.alpha = alpha;
-        r.hit_z = n_hit > 0 ? hit_sum / (double)n_hit : 0.0;
+        r.hit_z = hit_z;
         r.d1sq = (float)d1;
         r.n_hit = n_hit;
         recs[q] = r;
@@ -440,8 +455,8 @@ __global__ void __launch_bounds__(kKnnMaxThreads)
 
     const double minx = g->min_x, miny = g->min_y, cw = g->cw;
     const int nc = (int)g->n_col, nr = (int)g->n_row;
-    long long colw = (long long)floor(((double)qx - minx) / cw);
-    long long roww = (long long)floor(((double)qy - miny) / cw);
+    long long colw = gridk::cell_floor(qx, g->min_x_f, g->inv_cw_f, minx, cw);
+    long long roww = gridk::cell_floor(qy, g->min_y_f, g->inv_cw_f, miny, cw);
     const int col = (int)(colw < 0 ? 0 : (colw > nc - 1 ? nc - 1 : colw));
     const int row = (int)(roww < 0 ? 0 : (roww > nr - 1 ? nr - 1 : roww));
     const EdgeBounds eb = edge_bounds(qx, qy, g, col, row);
@@ -533,20 +548,19 @@ __global__ void __launch_bounds__(kKnnMaxThreads)
         n_hit += __shfl_xor_sync(full, n_hit, o);
         hit_sum += __shfl_xor_sync(full, hit_sum, o);
     }
-    double r_obs, mu;
+    double r_obs, alpha;
     if (F64) {
         r_obs = rs / (double)k;
         const double r_exp = ap.area_override > 0.0
                                  ? 1.0 / (2.0 * sqrt((double)g->n_data / ap.area_override))
                                  : g->r_exp;
-        mu = membership(nn_statistic(r_obs, r_exp), ap.r_min, ap.r_max);
+        const double mu = membership(nn_statistic(r_obs, r_exp), ap.r_min, ap.r_max);
+        alpha = decay_power(mu, ap.level[0], ap.level[1], ap.level[2], ap.level[3], ap.level[4]);
     } else {
         const float rf = (float)rs / (float)k;
         r_obs = rf;
-        mu = membership_f32(rf, g, ap);
+        alpha = decay_power_f32(membership_f32(rf, g, ap), ap.level_f);
     }
-    const double alpha =
-        decay_power(mu, ap.level[0], ap.level[1], ap.level[2], ap.level[3], ap.level[4]);
     const D d1 = __shfl_sync(full, md, 0);
     if (lane == 0) {
         if (J.recs) {

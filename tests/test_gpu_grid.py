@@ -55,6 +55,21 @@ def test_grid_duplicates_and_cell_boundaries(aidw, oracle):
         _compare(aidw, oracle, x, y, c)
 
 
+@pytest.mark.parametrize("cell_scale", [100 / 49, 50 / 49, 200 / 49, 1.0, 0.5])
+def test_grid_lattice_on_cell_edges(aidw, oracle, cell_scale):
+    # a 50 x 50 integer lattice has r_exp = 49 / 100, so these scales give
+    # cell widths at or within rounding of 1, 1/2, 2: most coordinates fall
+    # on a cell edge or within a float64 rounding of one, where the cell
+    # index must still equal the floor of the correctly rounded quotient
+    g = np.arange(50, dtype=np.float32)
+    x, y = np.meshgrid(g, g)
+    x, y = x.ravel(), y.ravel()
+    rng = np.random.default_rng(9)
+    extra = rng.integers(0, 2500, 700)
+    x, y = np.concatenate([x, x[extra]]), np.concatenate([y, y[extra]])
+    _compare(aidw, oracle, x, y, cell_scale)
+
+
 def test_grid_degenerate_boxes(aidw, oracle):
     x = np.linspace(0, 10, 1001, dtype=np.float32)
     _compare(aidw, oracle, x, np.zeros_like(x), 1.0)           # collinear
