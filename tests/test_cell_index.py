@@ -1,24 +1,27 @@
 """The cell index floor((x - minX) / cw) of the even grid (Sec. 3.2.2) is
-taken on the GPU as floor(a * fl(1/cw)) unless that product lies within
-2^-49 |q| of an integer, where the float64 division is used instead.  This
-checks, in float64 numpy arithmetic (IEEE, no fused operations), that the
-rule gives exactly floor of the correctly rounded quotient on random,
-lattice and near-edge inputs."""
+defined on float64 (the difference of the float32 inputs, correctly rounded
+quotient).  The GPU takes it in float32 - q = fl32(fl32(x - minX) *
+fl32(1/cw)) - unless q lies within 2^-21 |q| of an integer, where it falls
+back to the float64 division.  This checks, in IEEE float32 / float64 numpy
+arithmetic (no fused operations), that the rule gives exactly the defined
+floor on random, lattice and near-edge inputs, and that the fallback stays
+rare on ordinary data."""
 import numpy as np
 
 
-def _fast_floor(a, cw):
-    inv = 1.0 / cw
-    q = a * inv
+def _rule(x32, min32, cw):
+    inv = np.float32(1.0 / cw)
+    q = (x32 - min32) * inv                       # float32 sub, then float32 mul
     f = np.floor(q)
-    tol = np.abs(q) * 2.0 ** -49
-    near = ~((q - f > tol) & ((f + 1.0) - q > tol))
-    return np.where(near, np.floor(a / cw), f), near
+    tol = np.abs(q) * np.float32(2.0 ** -21)
+    near = ~(((q - f) > tol) & (((f + np.float32(1.0)) - q) > tol))
+    exact = np.floor((x32.astype(np.float64) - np.float64(min32)) / cw)
+    return np.where(near, exact, f.astype(np.float64)), exact, near
 
 
-def _check(a, cw):
-    got, near = _fast_floor(a, cw)
-    np.testing.assert_array_equal(got, np.floor(a / cw))
+def _check(x32, min32, cw):
+    got, exact, near = _rule(np.asarray(x32, np.float32), np.float32(min32), float(cw))
+    np.testing.assert_array_equal(got, exact)
     return near.mean()
 
 
@@ -26,25 +29,31 @@ def test_random_widths_and_offsets():
     rng = np.random.default_rng(0)
     for _ in range(200):
         cw = float(rng.uniform(1e-3, 10.0)) * 10.0 ** float(rng.integers(-3, 4))
-        a = rng.uniform(0.0, 5000.0 * cw, 20000).astype(np.float32).astype(np.float64)
-        assert _check(a, cw) < 1e-3
+        lo = np.float32(rng.uniform(-1000.0, 1000.0) * cw)
+        x = (lo + rng.uniform(0.0, 2000.0 * cw, 20000)).astype(np.float32)
+        x = np.maximum(x, lo)
+        assert _check(x, lo, cw) < 0.01
 
 
 def test_points_on_and_next_to_cell_edges():
-    rng = np.random.default_rng(1)
     for cw in (1.0, 0.5, 0.49, 0.1, 1.0 / 3.0, 0.49 * (100 / 49), 1000.0 / 1024.0):
-        k = np.arange(0, 4096, dtype=np.float64)
-        edge = k * cw
-        a = np.concatenate([edge, np.nextafter(edge, -np.inf), np.nextafter(edge, np.inf),
-                            edge.astype(np.float32).astype(np.float64)])
-        a = a[a >= 0.0]
-        _check(a, cw)
-        jitter = edge * (1.0 + rng.uniform(-4e-16, 4e-16, edge.size))
-        _check(jitter[jitter >= 0.0], cw)
+        edge = (np.arange(0, 4096, dtype=np.float64) * cw).astype(np.float32)
+        x = np.concatenate([edge, np.nextafter(edge, np.float32(-np.inf)),
+                            np.nextafter(edge, np.float32(np.inf))])
+        _check(x[x >= 0.0], np.float32(0.0), cw)
 
 
 def test_integer_lattice_with_unit_width_uses_the_division():
-    a = np.arange(0, 1000, dtype=np.float64)
-    got, near = _fast_floor(a, 1.0)
-    np.testing.assert_array_equal(got, a)
-    assert near[1:].all()          # exact integers always take the division
+    x = np.arange(0, 1000, dtype=np.float32)
+    got, exact, near = _rule(x, np.float32(0.0), 1.0)
+    np.testing.assert_array_equal(got, exact)
+    np.testing.assert_array_equal(got, np.arange(1000))
+    assert near.all()              # exact integers always take the division
+
+
+def test_uniform_data_rarely_falls_back():
+    rng = np.random.default_rng(2)
+    x = rng.uniform(0.0, 1000.0, 1 << 20).astype(np.float32)
+    lo = x.min()
+    cw = 2.0 * 1000.0 / (2.0 * np.sqrt(1 << 20))   # a typical cell width, 2 r_exp
+    assert _check(x, lo, cw) < 2e-3
