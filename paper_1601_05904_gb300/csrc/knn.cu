@@ -78,6 +78,26 @@ __device__ __forceinline__ int knn_job_of(const KnnJob *__restrict__ jobs, int n
     return lo;
 }
 
+// Sum of z over the points at distance 0 (the limit of Eq. 1 when a query
+// coincides with data): float64 in the float64 path; a TwoSum-compensated
+// float32 pair in the float32 path, so that the test on every candidate,
+// which the compiler may predicate rather than branch around, issues no
+// float64 instruction there.
+template <bool F64>
+struct HitSum;
+template <>
+struct HitSum<true> {
+    double s = 0.0;
+    __device__ __forceinline__ void add(float z) { s += (double)z; }
+    __device__ __forceinline__ double value() const { return s; }
+};
+template <>
+struct HitSum<false> {
+    float hi = 0.0f, lo = 0.0f;
+    __device__ __forceinline__ void add(float z) { comp_add(hi, lo, z); }
+    __device__ __forceinline__ double value() const { return (double)hi + (double)lo; }
+};
+
 // Stop-rule bounds.  The distance from the query to the outer edge of the
 // level-L block on one side is its distance to that edge of its own cell
 // plus L cell widths.  The four own-cell distances are lower bounds taken
@@ -244,7 +264,7 @@ __global__ void __launch_bounds__(kKnnMaxThreads)
     int kthi = 0x7fffffff;
     long long found = 0;
     int n_hit = 0;
-    double hit_sum = 0.0;
+    HitSum<F64> hits;
     int L0 = -1;  // paper rule: the first level whose block holds k points
 
     for (int L = 0;; ++L) {
@@ -282,7 +302,7 @@ __global__ void __launch_bounds__(kKnnMaxThreads)
                 const D d2 = DistT<F64>::d2(qx, qy, p.x, p.y);
                 if (d2 == (D)0) {
                     ++n_hit;
-                    hit_sum += (double)p.z;
+                    hits.add(p.z);
                 }
                 if (d2 < kth || (d2 == kth && pidx < kthi)) {
                     // replace the k-th and bubble the candidate down to its
@@ -339,7 +359,7 @@ __global__ void __launch_bounds__(kKnnMaxThreads)
         alpha = decay_power_f32(membership_f32(rf, g, ap), ap.level_f);
     }
     double hit_z = 0.0;
-    if (n_hit > 0) hit_z = hit_sum / (double)n_hit;
+    if (n_hit > 0) hit_z = hits.value() / (double)n_hit;
 
     D d1 = kd[KMAX - 1];  // the nearest, kd[lo]
 #pragma unroll
@@ -467,7 +487,7 @@ __global__ void __launch_bounds__(kKnnMaxThreads)
     int kthi = 0x7fffffff;
     long long found = 0;
     int n_hit = 0;
-    double hit_sum = 0.0;
+    HitSum<F64> hits;
     int L0 = -1;  // paper rule: the first level whose block holds k points
 
     for (int L = 0;; ++L) {
@@ -506,7 +526,7 @@ __global__ void __launch_bounds__(kKnnMaxThreads)
                     d2 = DistT<F64>::d2(qx, qy, p.x, p.y);
                     if (d2 == (D)0) {
                         ++n_hit;
-                        hit_sum += (double)p.z;
+                        hits.add(p.z);
                     }
                 }
                 unsigned m = __ballot_sync(full, d2 < kth || (d2 == kth && pidx < kthi));
@@ -543,6 +563,7 @@ __global__ void __launch_bounds__(kKnnMaxThreads)
 
     // Eq. 3-6 (the order of the r_obs sum differs from k_knn only in rounding)
     double rs = lane < k ? (F64 ? sqrt((double)md) : (double)sqrtf((float)md)) : 0.0;
+    double hit_sum = hits.value();
     for (int o = 16; o > 0; o >>= 1) {
         rs += __shfl_xor_sync(full, rs, o);
         n_hit += __shfl_xor_sync(full, n_hit, o);
