@@ -167,7 +167,9 @@ __device__ __forceinline__ long long cell_floor(float x, float min_f, float inv_
     const float q = __fmul_rn(__fsub_rn(x, min_f), inv_f);
     const float f = floorf(q);
     const float tol = fabsf(q) * 0x1p-21f;
-    if (q - f > tol && (f + 1.0f) - q > tol) return (long long)f;
+    // (a float32 -> int32 conversion saturates out of range; the caller
+    // clamps, and the int64 conversion would run on the float64 pipe)
+    if (q - f > tol && (f + 1.0f) - q > tol) return (long long)__float2int_rz(f);
     return (long long)floor(((double)x - min_d) / cw);
 }
 
