@@ -107,8 +107,8 @@ def workload_config(args, world, precision=None):
                         "alpha levels 1..5, R_min/R_max 0/2",
             "n_data": args.n, "n_query_per_gpu": args.n, "k": args.k,
             "precision": precision or "FP32-comp (SFU exp2/log2, TwoSum-compensated f32 "
-                                      "sums, f64 final divide; alpha from f32 sqrt/cos "
-                                      "with f64 sums)",
+                                      "sums, f64 final divide; alpha in f32 with a "
+                                      "compensated r_obs sum)",
             "l2": f"flushed between timed steps ({L2_FLUSH_BYTES >> 20} MiB write)",
             "parallelism": f"query-sharded x{world}" if world > 1 else "single GPU"}
 

@@ -49,8 +49,8 @@ typedef enum {
 /* Arithmetic of the kNN and weighting stages.
  *  AIDW_FP32_COMP  float32 distances, power by exp2(alpha*log2) on the SFU,
  *                  compensated float32 sums, float64 final divide; alpha
- *                  from float32 square roots (summed in float64) and a
- *                  float32 Eq. 4-5, Eq. 6 in float64.  Outputs are float32.
+ *                  from a compensated float32 sum of float32 square roots
+ *                  (Eq. 3) and Eq. 4-6 in float32.  Outputs are float32.
  *  AIDW_FP64_PLAIN float64 distances, pow(), plain float64 sums.  Outputs
  *                  are float64. */
 typedef enum { AIDW_FP32_COMP = 0, AIDW_FP64_PLAIN = 1 } aidw_precision;
