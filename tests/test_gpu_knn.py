@@ -105,12 +105,17 @@ def test_knn_argument_errors(aidw):
 
 
 @pytest.mark.slow
-def test_knn_full_size_sampled(aidw, oracle):
-    """1,048,576 uniform points and queries; the oracle checks a sample."""
-    w = inputs.uniform_kilo(seed=1)
-    idx, dist, robs = _knn(aidw, w.x, w.y, w.qx, w.qy, 10, 0.0 or 1.0)
+@pytest.mark.parametrize("kind,k", [("uniform", 10), ("clustered", 32), ("clustered", 8)])
+def test_knn_full_size_sampled(aidw, oracle, kind, k):
+    """1,048,576 points and queries at the automatic cell width for k (the
+    grid is built with the same k); the oracle checks a sample."""
+    w = inputs.uniform_kilo(seed=1) if kind == "uniform" else inputs.clustered_kilo(seed=2)
+    g = aidw.aidw_grid_build(dev(w.x), dev(w.y), dev(w.z), aidw.Params(k=k))
+    idx, dist, robs = (host(t) for t in aidw.aidw_knn(g, dev(w.qx), dev(w.qy), k))
+    assert aidw.aidw_grid_status(g) == 0
+    g.destroy()
     s = inputs.query_subsample(w.m, 256)
-    check_knn(oracle, w.x, w.y, w.qx[s], w.qy[s], 10, idx[s], dist[s], robs[s])
+    check_knn(oracle, w.x, w.y, w.qx[s], w.qy[s], k, idx[s], dist[s], robs[s])
 
 
 @pytest.mark.parametrize("k", [1, 10, 16, 32])
