@@ -116,13 +116,18 @@ __device__ __forceinline__ EdgeBounds edge_bounds(float qx, float qy, const Grid
 {
     // (at least the smallest normal float32: results flushed to zero are off
     // by less than that)
+    // (integer -> float conversions are rounded in the safe direction too,
+    // so the bounds hold for grids of more than 2^24 cells per side)
     const float margin = fmaxf(
-        __fmul_ru(__fmul_ru((float)(g->n_col + g->n_row + 2), g->cw_ru), 0x1p-50f), 0x1p-126f);
+        __fmul_ru(__fmul_ru(__ll2float_ru(g->n_col + g->n_row + 2), g->cw_ru), 0x1p-50f),
+        0x1p-126f);
     EdgeBounds e;
-    e.l = __fsub_rd(__fsub_rd(qx, __fmaf_ru((float)col, g->cw_ru, g->min_x_f)), margin);
-    e.r = __fsub_rd(__fsub_rd(__fmaf_rd((float)(col + 1), g->cw_rd, g->min_x_f), qx), margin);
-    e.b = __fsub_rd(__fsub_rd(qy, __fmaf_ru((float)row, g->cw_ru, g->min_y_f)), margin);
-    e.t = __fsub_rd(__fsub_rd(__fmaf_rd((float)(row + 1), g->cw_rd, g->min_y_f), qy), margin);
+    e.l = __fsub_rd(__fsub_rd(qx, __fmaf_ru(__int2float_ru(col), g->cw_ru, g->min_x_f)), margin);
+    e.r = __fsub_rd(__fsub_rd(__fmaf_rd(__int2float_rd(col + 1), g->cw_rd, g->min_x_f), qx),
+                    margin);
+    e.b = __fsub_rd(__fsub_rd(qy, __fmaf_ru(__int2float_ru(row), g->cw_ru, g->min_y_f)), margin);
+    e.t = __fsub_rd(__fsub_rd(__fmaf_rd(__int2float_rd(row + 1), g->cw_rd, g->min_y_f), qy),
+                    margin);
     e.cw = g->cw_rd;
     return e;
 }
@@ -336,7 +341,8 @@ __global__ void __launch_bounds__(kKnnMaxThreads)
             if (L0 >= 0 && L == L0 + 1) break;
             continue;
         }
-        if (found >= k && block_is_final(eb, (float)L, full_l, full_r, full_b, full_t, kth))
+        if (found >= k &&
+            block_is_final(eb, __int2float_rd(L), full_l, full_r, full_b, full_t, kth))
             break;
     }
 
@@ -557,7 +563,8 @@ __global__ void __launch_bounds__(kKnnMaxThreads)
             if (L0 >= 0 && L == L0 + 1) break;
             continue;
         }
-        if (found >= k && block_is_final(eb, (float)L, full_l, full_r, full_b, full_t, kth))
+        if (found >= k &&
+            block_is_final(eb, __int2float_rd(L), full_l, full_r, full_b, full_t, kth))
             break;
     }
 

@@ -57,6 +57,23 @@ def test_large_and_negative_coordinates(aidw, oracle, offset):
     check_knn(oracle, x, y, qx, qy, 12, host(idx), host(dist), host(robs))
 
 
+@pytest.mark.parametrize("cell_scale", [0.5, 1.0, 2.0])
+def test_stop_rule_at_coarse_float32_spacing(aidw, oracle, cell_scale):
+    # around 1e7 float32 coordinates are spaced 1.0 apart, a tenth of a cell
+    # here: the stop test's float32 edge bounds must stay lower bounds (an
+    # early stop would lose a neighbour the oracle's brute force finds)
+    rng = np.random.default_rng(54)
+    x, y = inputs.uniform_points(rng, 8000, 1.0e7, 1.0e7 + 1000.0)
+    qx, qy = inputs.uniform_points(rng, 2000, 1.0e7 - 50.0, 1.0e7 + 1050.0)
+    g = aidw.aidw_grid_build(dev(x), dev(y), dev(np.zeros_like(x)),
+                             aidw.Params(cell_scale=cell_scale))
+    for k in (1, 12, 32):
+        idx, dist, robs = aidw.aidw_knn(g, dev(qx), dev(qy), k)
+        check_knn(oracle, x, y, qx, qy, k, host(idx), host(dist), host(robs))
+    assert aidw.aidw_grid_status(g) == 0
+    g.destroy()
+
+
 def test_collinear_data_zero_area(aidw, oracle):
     rng = np.random.default_rng(53)
     y = rng.uniform(0, 100, 3000).astype(np.float32)
