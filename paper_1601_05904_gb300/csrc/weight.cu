@@ -51,7 +51,15 @@ namespace {
 constexpr int kDTile = 1024;   // points per shared-memory stage
 static_assert(kDTile == kWeightTile, "weighting tiles are staged whole");
 constexpr int kStages = 3;
-constexpr int kChunk = 32;     // points per plain float32 partial sum (per lane)
+// Points per plain float32 partial sum (per lane) before it is folded into
+// the TwoSum-compensated total.  A plain sum of n positive terms is within
+// (n - 1) * 2^-24 of its magnitude, so with 64 the error budget of a
+// prediction (numerator and denominator) stays under 2 * 63 * 2^-24 = 7.5e-6
+// of S_q (the normalised measure) plus the SFU approximation errors, inside
+// the 1e-5 bound; measured on GB300 at n = m = 1M (weighting ms, unroll of
+// the point loop): chunk 32 / unroll 4: 352.3, 64 / 4: 345.4, 64 / 8:
+// 341.6, 64 / 16: 334.5, 64 / 32: 389.3, 32 / 16: 346.9, 16 / 4: 367.0.
+constexpr int kChunk = 64;
 constexpr int kChunk2 = 2 * kChunk;
 constexpr int kWaitTries = 2000;  // tries of up to ~1 ms: a data-tile wait gives up after ~2 s
 
@@ -250,7 +258,7 @@ __global__ void __launch_bounds__(THREADS, MINB)
                     F2 ps[Q], pz[Q];
 #pragma unroll
                     for (int i = 0; i < Q; ++i) ps[i] = pz[i] = zero2;
-#pragma unroll 4
+#pragma unroll 16
                     for (int jj = c0; jj < c0 + kChunk2; jj += 4) {
                         const float4 xv = *reinterpret_cast<const float4 *>(X + jj);
                         const float4 yv = *reinterpret_cast<const float4 *>(Y + jj);
@@ -471,9 +479,9 @@ __global__ void k_finalize_f64(SKArgs a, const double2 *__restrict__ part)
 
 // Polynomial split of the float32 kernel: products per inner step whose exp2
 // (first number) and lg2 (second) run on the FMA pipe.  Measured on GB300 at
-// n = m = 1M (weighting ms): {2,0} 353.9, {0,0} 367.9, {3,0} 377.5,
-// {4,0} 395, {0,1} 357.5, {1,1} 358.7, {0,2} 377.5, {2,1} 393.2, so {2,0} is
-// the default.  AIDW_WEIGHT_POLY ("E,L") selects another entry of the table,
+// n = m = 1M (weighting ms, 64-point chunks, point loop unrolled 16x):
+// {2,0} 334.8, {0,0} 352.4, {3,0} 354.8, {4,0} 382.1, {0,1} 345.3,
+// {1,1} 348.3, {0,2} 369.2, so {2,0} is the default.  AIDW_WEIGHT_POLY ("E,L") selects another entry of the table,
 // for measuring the balance on a given GPU.
 using F32Kernel = void (*)(SKArgs, float4 *);
 struct PolySplit {

@@ -71,7 +71,10 @@ def test_graph_replay_with_new_buffers(aidw, oracle):
     plan.destroy()
 
 
-def test_autotuner_keeps_results(aidw):
+def test_autotuner_keeps_results(aidw, oracle):
+    """Retuning changes the cell width and kNN shape, hence the rounding
+    order of the sums only: before and after, every job is within the
+    float32 tolerance of the oracle."""
     p = aidw.Params(k=10)
     jobs, raw = _jobs(aidw, [(20000, 4000, 10, 0.9), (5000, 3000, 24, 0.0)] * 3, seed=4)
     plan = aidw.aidw_batch_plan_create(jobs, p)
@@ -84,8 +87,10 @@ def test_autotuner_keeps_results(aidw):
         j.out_z = None
     after = [host(o) for o in aidw.aidw_batch_run(plan, jobs)]
     assert aidw.aidw_batch_plan_status(plan) == 0
-    for a, b, r in zip(before, after, raw):
-        np.testing.assert_allclose(a, b, rtol=0, atol=2e-6 * np.abs(r[2]).max())
+    for a, b, (x, y, z, qx, qy, k) in zip(before, after, raw):
+        ref = oracle.aidw(x, y, z, qx, qy, k)
+        for out in (a, b):
+            assert oracle.normalized_error(out, ref["z"], ref["scale"]).max() <= TOL_FP32
     plan.destroy()
 
 
