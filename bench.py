@@ -521,7 +521,7 @@ PAPER_SIZES = (10240, 51200, 102400, 512000, 1024000)  # 10K .. 1000K with 1K = 
 # DRAM bytes (read + write) of one k_weight_f32 launch per data point, from
 # the ncu capture at n = m = 131,072 (5.80 MB read, 0 written); every input
 # (points, queries, kNN records) is read once, so it scales with n = m.
-WEIGHT_DRAM_BYTES_PER_POINT = 5.801984e6 / 131072
+WEIGHT_DRAM_BYTES_PER_POINT = 5.82144e6 / 131072
 
 
 def _time_ms(fn, reps):
