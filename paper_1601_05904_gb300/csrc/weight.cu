@@ -14,11 +14,13 @@
 // queries one job after the other; a CTA finds the job of a unit by binary
 // search in the job table, so one launch balances jobs of any sizes.
 //
-// Data staging.  Each data tile is one contiguous run of 16-byte points; one
-// elected thread streams it into shared memory with a bulk (TMA) copy that
-// completes on an mbarrier, kStages tiles ahead.  Every thread then reads
-// each point as a broadcast 16-byte shared load and applies it to its kQPT
-// queries held in registers.
+// Data staging.  One elected thread streams each data tile into shared
+// memory with bulk (TMA) copies that complete on an mbarrier, kStages tiles
+// ahead.  The float32 path stages a tile as three cell-ordered arrays
+// (-x, -y, z); every thread reads four consecutive values of each with one
+// broadcast 16-byte shared load and applies them, two points per packed
+// f32x2 instruction, to its kQPT queries held in registers.  The float64
+// path stages the tile as one run of 16-byte points.
 //
 // Float32 path (AIDW_FP32_COMP).  With d1^2 the smallest squared distance of
 // the query (from the kNN stage, computed by the same float32 code):
@@ -26,9 +28,11 @@
 //     c = -alpha/2, b = -c * log2(d1^2)
 // which is Eq. 1's weight d^-alpha multiplied by d1^alpha (cancels in the
 // ratio) and is at most 1, so nothing overflows.  log2 and exp2 are the SFU
-// approximations.  Sums over kChunk points are plain float32; the chunk sums
-// are added into a (hi, lo) pair with TwoSum, and the final ratio is formed
-// in float64.
+// approximations, except for a fixed share of the exp2s (and, as an option,
+// log2s) evaluated by polynomials on the FMA pipe to balance the two pipes.
+// Sums over kChunk points per lane are plain float32; the chunk sums are
+// added into a (hi, lo) pair with TwoSum, and the final ratio is formed in
+// float64.
 //
 // Float64 path (AIDW_FP64_PLAIN): w = pow(d^2, -alpha/2) in float64, plain
 // float64 sums, same decomposition.
