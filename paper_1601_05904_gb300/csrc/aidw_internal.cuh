@@ -44,7 +44,7 @@ struct __align__(16) Point { float x, y, z; int idx; };
 // as tiles of kWeightTile {-x[], -y[], z[]} float32 arrays (structure of
 // arrays inside a tile, negated coordinates so that q + (-p) == q - p), which
 // the weighting kernel streams into shared memory one tile per bulk copy.
-constexpr int kWeightTile = 1024;
+constexpr int kWeightTile = 2048;
 
 // Per-query result of the kNN stage consumed by the weighting stage.
 struct QRec {

@@ -52,7 +52,7 @@ namespace aidw {
 
 namespace {
 
-constexpr int kDTile = 1024;   // points per shared-memory stage
+constexpr int kDTile = 2048;   // points per shared-memory stage
 static_assert(kDTile == kWeightTile, "weighting tiles are staged whole");
 constexpr int kStages = 3;
 // Points per plain float32 partial sum (per lane) before it is folded into
