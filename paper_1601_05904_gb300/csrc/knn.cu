@@ -312,17 +312,18 @@ __global__ void __launch_bounds__(kKnnMaxThreads)
                 if (d2 < kth || (d2 == kth && pidx < kthi)) {
                     // replace the k-th and bubble the candidate down to its
                     // place.  Once it stops, no later step swaps, so the exit
-                    // test may be skipped: every step for up to 16 slots,
-                    // every fourth step for 32 (an exit on every one of 31
-                    // steps costs registers and diverges, measured 2x slower;
-                    // none at all, 1.2-1.5x slower at k = 20..32)
+                    // test may be skipped on some steps: it is taken on every
+                    // second step for up to 16 slots and every fourth for 32
+                    // (measured at 1M: on every step, k = 10 0.70 vs 0.57 ms;
+                    // for 32 slots on every step, 2x slower; never, 1.2-1.5x
+                    // slower at k = 20..32)
                     kd[KMAX - 1] = d2;
                     ki[KMAX - 1] = pidx;
 #pragma unroll
                     for (int j = KMAX - 1; j > 0; --j) {
                         const bool sw =
                             kd[j] < kd[j - 1] || (kd[j] == kd[j - 1] && ki[j] < ki[j - 1]);
-                        if ((KMAX <= 16 || (j & 3) == 0) && !sw) break;
+                        if ((j & (KMAX <= 16 ? 1 : 3)) == 0 && !sw) break;
                         const D td = kd[j], tl = kd[j - 1];
                         const int ti = ki[j], tj = ki[j - 1];
                         kd[j] = sw ? tl : td;
