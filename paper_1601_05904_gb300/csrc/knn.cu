@@ -399,29 +399,53 @@ __global__ void __launch_bounds__(kKnnMaxThreads)
             static_cast<float *>(out_alpha)[q] = (float)alpha;
     }
     if (J.out_zlocal) {
-        // Eq. 1 over the k neighbours: weights (d^2 / d1^2)^(-alpha/2) (float32
-        // path, SFU, largest weight 1) or pow(d^2, -alpha/2) (float64 path),
-        // sums in float64; coincident neighbours give their mean z.
-        const float c = (float)(-0.5 * alpha);
-        const float b = F64 ? 0.0f : -c * lg2_sfu((float)d1);
-        double sw = 0.0, swz = 0.0, hz = 0.0;
-        int nh = 0;
+        // Eq. 1 over the k neighbours; coincident neighbours give their mean
+        // z.  Float64 path: pow(d^2, -alpha/2) and float64 sums.  Float32
+        // path: weights (d^2 / d1^2)^(-alpha/2) on the SFU (largest weight 1)
+        // and TwoSum-compensated float32 sums of at most 32 terms (float64
+        // adds would cost more than the whole search on this GPU), one
+        // float64 division at the end.
+        double zl;
+        if (F64) {
+            double sw = 0.0, swz = 0.0, hz = 0.0;
+            int nh = 0;
 #pragma unroll
-        for (int j = 0; j < KMAX; ++j) {
-            if (j >= lo) {
-                const double zj = (double)J.zorig[ki[j]];
-                if (kd[j] == (D)0) {
-                    ++nh;
-                    hz += zj;
-                } else {
-                    const double w = F64 ? pow((double)kd[j], -0.5 * alpha)
-                                         : (double)ex2_sfu(fma_rn(lg2_sfu((float)kd[j]), c, b));
-                    sw += w;
-                    swz += w * zj;
+            for (int j = 0; j < KMAX; ++j) {
+                if (j >= lo) {
+                    const double zj = (double)J.zorig[ki[j]];
+                    if (kd[j] == (D)0) {
+                        ++nh;
+                        hz += zj;
+                    } else {
+                        const double w = pow((double)kd[j], -0.5 * alpha);
+                        sw += w;
+                        swz += w * zj;
+                    }
                 }
             }
+            zl = nh ? hz / (double)nh : swz / sw;
+        } else {
+            const float c = (float)(-0.5 * alpha);
+            const float b = -c * lg2_sfu((float)d1);
+            float swh = 0.0f, swl = 0.0f, szh = 0.0f, szl = 0.0f, hzh = 0.0f, hzl = 0.0f;
+            int nh = 0;
+#pragma unroll
+            for (int j = 0; j < KMAX; ++j) {
+                if (j >= lo) {
+                    const float zj = J.zorig[ki[j]];
+                    if (kd[j] == (D)0) {
+                        ++nh;
+                        comp_add(hzh, hzl, zj);
+                    } else {
+                        const float w = ex2_sfu(fma_rn(lg2_sfu((float)kd[j]), c, b));
+                        comp_add(swh, swl, w);
+                        comp_add(szh, szl, mul_rn(w, zj));
+                    }
+                }
+            }
+            zl = nh ? ((double)hzh + (double)hzl) / (double)nh
+                    : ((double)szh + (double)szl) / ((double)swh + (double)swl);
         }
-        const double zl = nh ? hz / (double)nh : swz / sw;
         if (F64)
             static_cast<double *>(J.out_zlocal)[q] = zl;
         else
