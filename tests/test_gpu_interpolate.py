@@ -157,19 +157,19 @@ def test_nonfinite_query(aidw):
 
 
 @pytest.mark.slow
-@pytest.mark.parametrize("kind", ["uniform", "clustered"])
-def test_full_size_sampled(aidw, oracle, kind):
+@pytest.mark.parametrize("kind,k", [("uniform", 10), ("clustered", 10), ("clustered", 20)])
+def test_full_size_sampled(aidw, oracle, kind, k):
     """n = m = 1,048,576 in [0,1000]^2 with every query on the GPU; the oracle
     checks a sample of 256 (float32 path) and the float64 path runs on a
     sample of 4096 queries."""
     w = inputs.uniform_kilo(seed=1) if kind == "uniform" else inputs.clustered_kilo(seed=2)
-    zq, al = _interp(aidw, w.x, w.y, w.z, w.qx, w.qy, 10)
+    zq, al = _interp(aidw, w.x, w.y, w.z, w.qx, w.qy, k)
     s = inputs.query_subsample(w.m, 256)
-    _check(oracle, w.x, w.y, w.z, w.qx[s], w.qy[s], 10, zq[s], al[s], TOL_FP32, 1e-5)
+    _check(oracle, w.x, w.y, w.z, w.qx[s], w.qy[s], k, zq[s], al[s], TOL_FP32, 1e-5)
     s64 = inputs.query_subsample(w.m, 4096, seed=77)
-    z64, a64 = _interp(aidw, w.x, w.y, w.z, w.qx[s64], w.qy[s64], 10, fp64=True)
+    z64, a64 = _interp(aidw, w.x, w.y, w.z, w.qx[s64], w.qy[s64], k, fp64=True)
     s2 = np.arange(0, 4096, 32)
-    _check(oracle, w.x, w.y, w.z, w.qx[s64][s2], w.qy[s64][s2], 10, z64[s2], a64[s2],
+    _check(oracle, w.x, w.y, w.z, w.qx[s64][s2], w.qy[s64][s2], k, z64[s2], a64[s2],
            TOL_FP64, 1e-9)
 
 
