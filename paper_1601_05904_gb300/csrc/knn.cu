@@ -114,10 +114,10 @@ struct EdgeBounds {
 __device__ __forceinline__ EdgeBounds edge_bounds(float qx, float qy, const GridDev *g, int col,
                                                   int row)
 {
-    // (at least the smallest normal float32: results flushed to zero are off
-    // by less than that)
-    // (integer -> float conversions are rounded in the safe direction too,
-    // so the bounds hold for grids of more than 2^24 cells per side)
+    // The margin is at least the smallest normal float32 (results flushed to
+    // zero are off by less than that); integer -> float conversions are
+    // rounded in the safe direction too, so the bounds also hold for grids
+    // of more than 2^24 cells per side.
     const float margin = fmaxf(
         __fmul_ru(__fmul_ru(__ll2float_ru(g->n_col + g->n_row + 2), g->cw_ru), 0x1p-50f),
         0x1p-126f);
