@@ -83,6 +83,15 @@ def max_over_ranks(seconds: float, device=None) -> float:
     return float(t.item())
 
 
+def host_cores() -> int:
+    """Cores this process may run on; the oracle legs use all of them (a
+    launcher may set OMP_NUM_THREADS=1 per rank, which they override)."""
+    try:
+        return len(os.sched_getaffinity(0))
+    except (AttributeError, OSError):
+        return os.cpu_count() or 1
+
+
 def whole_job_value(world: int, units_per_rank: int, steps: int, seconds: float) -> float:
     """Units processed by all ranks over the timed steps, per second of the
     slowest rank (weak scaling: every rank has the same amount of work)."""
@@ -186,16 +195,16 @@ def cpu_baseline(w, seconds: float, rank: int, local: bool = False):
     from paper_1601_05904_gb300 import inputs
     oracle.build()
     fn = oracle.aidw_local if local else oracle.aidw
-    cores = oracle.num_threads()
+    cores = host_cores() if oracle.has_openmp() else 1
     probe = max(cores, 8)
     s = inputs.query_subsample(w.m, probe, seed=2024 + rank)
     t0 = time.perf_counter()
-    fn(w.x, w.y, w.z, w.qx[s], w.qy[s], w.k)
+    fn(w.x, w.y, w.z, w.qx[s], w.qy[s], w.k, nthreads=cores)
     per_q = (time.perf_counter() - t0) / probe
     count = int(max(probe, min(w.m, seconds / max(per_q, 1e-9))))
     s = inputs.query_subsample(w.m, count, seed=4048 + rank)
     t0 = time.perf_counter()
-    ref = fn(w.x, w.y, w.z, w.qx[s], w.qy[s], w.k)
+    ref = fn(w.x, w.y, w.z, w.qx[s], w.qy[s], w.k, nthreads=cores)
     dt = time.perf_counter() - t0
     return ({"value": count / dt, "unit": UNIT, "cores": cores, "kind": "oracle",
              "sample": f"{count} of {w.m} queries against all {w.n} data points "
@@ -236,16 +245,16 @@ def run_reference(args):
     import oracle
     from paper_1601_05904_gb300 import inputs
     oracle.build()
-    cores = oracle.num_threads()
+    cores = host_cores() if oracle.has_openmp() else 1
     per_step = max(cores, 16)
     for i in range(args.warmup):
         s = inputs.query_subsample(w.m, per_step, seed=500 + i)
-        oracle.aidw(w.x, w.y, w.z, w.qx[s], w.qy[s], w.k)
+        oracle.aidw(w.x, w.y, w.z, w.qx[s], w.qy[s], w.k, nthreads=cores)
     times = []
     for i in range(args.steps):
         s = inputs.query_subsample(w.m, per_step, seed=900 + i)
         t0 = time.perf_counter()
-        oracle.aidw(w.x, w.y, w.z, w.qx[s], w.qy[s], w.k)
+        oracle.aidw(w.x, w.y, w.z, w.qx[s], w.qy[s], w.k, nthreads=cores)
         times.append(time.perf_counter() - t0)
     total = sum(times)
     value = per_step * args.steps / total
@@ -355,14 +364,16 @@ def run_ours(args):
         host = {k: torch.from_numpy(getattr(w, k)).pin_memory() for k in ("x", "y", "z", "qx", "qy")}
         binding.interpolate_host(host["x"], host["y"], host["z"], host["qx"], host["qy"], params)
         torch.cuda.synchronize()
+        if world > 1:
+            torch.distributed.barrier()
         t0 = time.perf_counter()
         for _ in range(args.e2e_steps):
             zh = binding.interpolate_host(host["x"], host["y"], host["z"], host["qx"],
                                           host["qy"], params)
             float(zh[0])
-        e2e_s = time.perf_counter() - t0
+        e2e_s = max_over_ranks(time.perf_counter() - t0, dev)
         h2d = sum(v.numel() * 4 for v in host.values())
-        e2e = {"value": w.m * args.e2e_steps / e2e_s, "unit": UNIT,
+        e2e = {"value": whole_job_value(world, w.m, args.e2e_steps, e2e_s), "unit": UNIT,
                "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(w.m * 4),
                "ms_per_step": 1000.0 * e2e_s / args.e2e_steps}
 
@@ -410,7 +421,7 @@ def run_ours(args):
     stages_ms = {k: v[0] / args.steps for k, v in stage.items()}
     cpu = None
     accuracy = None
-    if not args.no_cpu_baseline and world >= 1:
+    if not args.no_cpu_baseline and world == 1:     # the oracle on rank 0 at N = 1 only
         cpu, sample, ref = cpu_baseline(w, args.cpu_seconds, rank, local=args.mode == "local")
         if args.mode in ("aidw", "local"):
             accuracy = accuracy_on_sample(binding, pkg, t, w, sample, ref, params,

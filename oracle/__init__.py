@@ -92,6 +92,8 @@ def _load():
         lib.oracle_alpha.argtypes = [ctypes.c_double, c_d]
         lib.oracle_num_threads.restype = ctypes.c_int
         lib.oracle_num_threads.argtypes = []
+        lib.oracle_has_openmp.restype = ctypes.c_int
+        lib.oracle_has_openmp.argtypes = []
         lib.oracle_knn.restype = None
         lib.oracle_knn.argtypes = [c_f, c_f, i64, c_f, c_f, i64, ctypes.c_int,
                                    c_i32, c_d, ctypes.c_int]
@@ -127,6 +129,11 @@ def _f32(a) -> np.ndarray:
 def num_threads() -> int:
     """Threads the oracle's query loop uses by default (1 without OpenMP)."""
     return int(_load().oracle_num_threads())
+
+
+def has_openmp() -> bool:
+    """Whether the query loops can run on several threads (``nthreads``)."""
+    return bool(_load().oracle_has_openmp())
 
 
 def r_exp(n: int, area: float) -> float:

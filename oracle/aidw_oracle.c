@@ -139,6 +139,16 @@ static void oracle_knn_one(const float *x, const float *y, int64_t n,
     }
 }
 
+/* 1 when the query loops run in parallel (compiled with OpenMP), else 0. */
+int oracle_has_openmp(void)
+{
+#ifdef _OPENMP
+    return 1;
+#else
+    return 0;
+#endif
+}
+
 int oracle_num_threads(void)
 {
 #ifdef _OPENMP

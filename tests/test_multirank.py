@@ -62,3 +62,27 @@ def test_two_ranks_share_data_shard_queries_and_take_the_slowest_time():
         assert q0 != q1          # each rank its own queries
         assert t == 2.0          # max over ranks
         assert value == pytest.approx(2 * 4096 * 3 / 2.0)
+
+
+def test_reference_arm_under_torchrun_prints_one_line_from_rank_zero(tmp_path):
+    """`bench.py --impl reference` launched as two ranks: rank 0 alone times
+    the oracle (on all of the host's cores, although the launcher sets
+    OMP_NUM_THREADS=1 per rank) and prints the one JSON line; the other rank
+    exits 0 without work."""
+    import json
+    import subprocess
+    cmd = [sys.executable, "-m", "torch.distributed.run", "--nnodes=1", "--nproc-per-node", "2",
+           "--master-addr", "127.0.0.1", "--master-port", str(_free_port()),
+           os.path.join(ROOT, "bench.py"), "--impl", "reference", "--gpus", "2",
+           "--steps", "1", "--warmup", "0"]
+    r = subprocess.run(cmd, capture_output=True, text=True, timeout=600, cwd=str(tmp_path))
+    assert r.returncode == 0, r.stderr[-2000:]
+    lines = [json.loads(l) for l in r.stdout.splitlines() if l.startswith("{")]
+    assert len(lines) == 1
+    d = lines[0]
+    assert d["impl"] == "reference" and d["n_gpus"] == 2 and d["value"] > 0
+    assert d["cpu_baseline"]["kind"] == "oracle"
+    assert d["e2e"]["h2d_bytes_per_step"] == 0 and d["e2e"]["d2h_bytes_per_step"] == 0
+    import oracle
+    if oracle.has_openmp():
+        assert d["cpu_baseline"]["cores"] == len(os.sched_getaffinity(0))
