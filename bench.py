@@ -20,6 +20,7 @@ method has) on the host cores, each step a bounded sample of the queries.
 from __future__ import annotations
 
 import argparse
+import gc
 import json
 import os
 import statistics
@@ -319,6 +320,7 @@ def run_ours(args):
     torch.cuda.synchronize()
     clocks.start()
     binding.aidw_profile_enable(True)
+    gc.disable()   # no collection between a step's synchronous status read and its launches
     t_wall = time.perf_counter()
     for i in range(args.steps):
         flush.fill_(float(i))
@@ -327,6 +329,7 @@ def run_ours(args):
         ev[i][1].record()
     torch.cuda.synchronize()
     wall = time.perf_counter() - t_wall
+    gc.enable()
     binding.aidw_profile_enable(False)
     if world > 1:
         torch.distributed.barrier()
@@ -478,12 +481,14 @@ def run_batch(args):
         torch.distributed.barrier()
     torch.cuda.synchronize()
     clocks.start()
+    gc.disable()
     for i in range(args.steps):
         flush.fill_(float(i))
         ev[i][0].record()
         binding.aidw_batch_run(plan, jobs)
         ev[i][1].record()
     torch.cuda.synchronize()
+    gc.enable()
     if world > 1:
         torch.distributed.barrier()
     clk = clocks.stop()
