@@ -158,6 +158,39 @@ aidw_status aidw_interpolate(const aidw_grid *g, const float *qx, const float *q
                              int64_t n_query, const aidw_params *p, void *out_z,
                              void *out_alpha, aidw_stream_t stream);
 
+/* ---- query sharding over several GPUs --------------------------------------
+ * Every query is computed independently given all data points (the
+ * one-thread-per-query decomposition of Sec. 4.2), so one query set splits
+ * over G GPUs with no exchange on the data path: each GPU (one process per
+ * GPU) builds its own grid from a replica of the data points, interpolates
+ * one contiguous slice of the queries, and writes that slice of the output.
+ * No counterpart in the paper, which runs on one GPU. */
+
+/* The slice [*begin, *end) of a query set of n_query queries that shard
+ * `shard` of `n_shards` takes: contiguous slices in shard order whose sizes
+ * differ by at most one (the first n_query % n_shards shards take one query
+ * more).  Host only: no CUDA call.  AIDW_ERR_INVALID_ARG for a null output,
+ * n_query < 0, n_shards < 1 or shard outside [0, n_shards). */
+aidw_status aidw_shard_range(int64_t n_query, int shard, int n_shards, int64_t *begin,
+                             int64_t *end);
+
+/* One shard of a query-sharded interpolation: aidw_interpolate of the
+ * queries [begin, end) = aidw_shard_range(n_query, shard, n_shards) on the
+ * current device, against grid g (built on this device from the full data
+ * set).  qx, qy are the FULL query arrays [n_query] and out_z (out_alpha, if
+ * not NULL) full-length output arrays [n_query] of the precision's element
+ * type, all device memory on this device; only elements [begin, end) of the
+ * outputs are written.  The shards of all GPUs together write every output
+ * element exactly once; bringing the slices together (if one process needs
+ * them all) is the caller's.  Per-query results equal those of
+ * aidw_interpolate on the whole set to rounding (the all-points sums of
+ * Eq. 1 may be grouped differently).  Errors as aidw_interpolate, plus
+ * AIDW_ERR_INVALID_ARG for a bad shard. */
+aidw_status aidw_interpolate_shard(const aidw_grid *g, const float *qx, const float *qy,
+                                   int64_t n_query, int shard, int n_shards,
+                                   const aidw_params *p, void *out_z, void *out_alpha,
+                                   aidw_stream_t stream);
+
 /* ---- batched interpolation ------------------------------------------------
  * Many independent AIDW problems ("jobs"), each with its own data points,
  * queries and k, computed together: the method of the functions above
@@ -223,18 +256,27 @@ aidw_status aidw_batch(const aidw_job *jobs, int n_jobs, const aidw_params *p,
  * the GPU's memory up front and hands out slices from its own pool, or a
  * latency-critical loop where cudaMalloc/cudaFree (which may synchronise the
  * device, or fail under memory pressure halfway through a pipeline) is not
- * acceptable.  aidw_interpolate_noalloc computes exactly what
- * aidw_interpolate computes, but keeps its per-call scratch (the per-query
- * kNN records and the partial sums of the weighting stage) in one
- * fixed-size array inside the library's device image, so the call performs
- * no allocation of any kind.  The caller still passes the grid, the queries
+ * acceptable.  aidw_interpolate_noalloc gives the predictions (and alphas)
+ * of aidw_interpolate, but keeps its per-call scratch (the per-query kNN
+ * records and the partial sums of the weighting stage) in one fixed-size
+ * array inside the library's device image, so the call performs no
+ * allocation of any kind.  The caller still passes the grid, the queries
  * and the outputs.
+ *  - It runs the kNN and weighting kernels of aidw_interpolate but not the
+ *    pass that first orders the queries by grid cell (its temporaries would
+ *    need memory): the kNN takes the queries in input order, which gives
+ *    the same results and is slower on clustered data.
  *  - n_query must not exceed AIDW_NOALLOC_MAX_QUERIES; larger calls return
  *    AIDW_ERR_INVALID_ARG and enqueue nothing.
  *  - The scratch array (AIDW_NOALLOC_SCRATCH_BYTES) lives in every GPU that
  *    loads the library until the process exits.
  *  - The first call on a device looks up the array's device address (host
- *    set-up); make that first call before any stream capture.
+ *    set-up); make that first call before any stream capture.  A first call
+ *    on a stream that is being captured returns AIDW_ERR_INVALID_ARG and
+ *    enqueues nothing.
+ *  - If a weighting wait expires (aidw_grid_status then reports
+ *    AIDW_ERR_TIMEOUT), the queries whose sums were left incomplete get NaN
+ *    predictions, as in aidw_interpolate.
  *  - Every call on a device shares the one array: calls that can overlap on
  *    the GPU (different streams, no ordering between them) race on it.
  *    Calls ordered on one stream are safe.  Nothing in the array needs to
@@ -295,10 +337,11 @@ aidw_status aidw_set_memory_limit(int64_t bytes, int64_t *held);
  * batch run; a launch being captured into a graph leaves the hook for the
  * next one) leaves the copy of one data tile unissued and bounds its waits
  * at `tries` (1..2000) tries, so the CTA that needs that tile gives up: it
- * latches AIDW_ERR_TIMEOUT, waits (bounded) for its own copies in flight
- * and returns.  The GPU stays usable; that call's predictions are
- * undefined; aidw_grid_status (or aidw_batch_plan_status) reports the
- * timeout. */
+ * latches AIDW_ERR_TIMEOUT, waits (bounded) for its own copies in flight,
+ * marks the partial sums it had not finished as NaN and returns.  The GPU
+ * stays usable; the queries whose sums that CTA had not finished get NaN
+ * predictions, the others are computed normally; aidw_grid_status (or
+ * aidw_batch_plan_status) reports the timeout. */
 aidw_status aidw_test_expire_next_wait(int tries);
 
 /* Short English name of a status code (static storage). */
@@ -330,6 +373,20 @@ aidw_status aidw_profile_read(double *ms, int64_t *launches);
  * as the denominator of the weighting kernel's roofline. */
 aidw_status aidw_probe_pipe_rates(double *lg2_per_sm_clk, double *ex2_per_sm_clk,
                                   double *ffma2_lanes_per_sm_clk);
+
+/* Instruction mix of the float32 weighting loop (AIDW_FP32_COMP) that this
+ * library launches, for roofline accounting (no counterpart in the paper).
+ * Every (query, data point) pair needs one log2 and one exp2; of every
+ * *products pairs of the loop's inner step, *poly_exp2 take the exp2 and
+ * *poly_lg2 the log2 from float32 polynomials on the FMA pipe instead of
+ * the SFU.  fma_lanes[3] receives the FMA-pipe lane operations per pair of
+ * the base loop, of one exp2 polynomial and of one log2 polynomial;
+ * instr[3] the instructions per pair of the same three parts, not counting
+ * the SFU instructions, loads and loop control (a packed two-lane
+ * instruction counts as half an instruction per pair).  Any pointer may be
+ * NULL.  Host only: no CUDA call. */
+aidw_status aidw_weight_mix(int *products, int *poly_exp2, int *poly_lg2, double *fma_lanes,
+                            double *instr);
 
 #ifdef __cplusplus
 }

@@ -134,6 +134,14 @@ def load(path: str | None = None):
         lib.aidw_profile_read.argtypes = [P(ctypes.c_double), P(ctypes.c_int64)]
         lib.aidw_probe_pipe_rates.restype = c_int
         lib.aidw_probe_pipe_rates.argtypes = [P(ctypes.c_double)] * 3
+        lib.aidw_shard_range.restype = c_int
+        lib.aidw_shard_range.argtypes = [i64, c_int, c_int, P(i64), P(i64)]
+        lib.aidw_interpolate_shard.restype = c_int
+        lib.aidw_interpolate_shard.argtypes = [vp, vp, vp, i64, c_int, c_int, P(CParams), vp,
+                                               vp, vp]
+        lib.aidw_weight_mix.restype = c_int
+        lib.aidw_weight_mix.argtypes = [P(c_int), P(c_int), P(c_int), P(ctypes.c_double),
+                                        P(ctypes.c_double)]
         lib.aidw_batch_plan_create.restype = c_int
         lib.aidw_batch_plan_create.argtypes = [P(CJob), c_int, P(CParams), P(vp)]
         lib.aidw_batch_run.restype = c_int
@@ -331,6 +339,42 @@ def aidw_interpolate_local(grid: Grid, qx, qy, params: Params | None = None, out
     return out_z, out_alpha
 
 
+def aidw_shard_range(n_query: int, shard: int, n_shards: int) -> tuple[int, int]:
+    """Query slice [begin, end) of shard ``shard`` of ``n_shards`` (host only)."""
+    b, e = ctypes.c_int64(), ctypes.c_int64()
+    _check(load().aidw_shard_range(int(n_query), int(shard), int(n_shards), ctypes.byref(b),
+                                   ctypes.byref(e)), "aidw_shard_range")
+    return b.value, e.value
+
+
+def aidw_interpolate_shard(grid: Grid, qx, qy, shard: int, n_shards: int,
+                           params: Params | None = None, out_z=None, out_alpha=None,
+                           want_alpha: bool = False, stream=None):
+    """Interpolates this shard's slice of the full query set (qx, qy) into
+    full-length outputs; elements outside the slice are left as they were.
+    Returns (z, alpha | None) full-length."""
+    import torch
+    p = params or Params()
+    qx, qy = _f32_dev(qx, "qx"), _f32_dev(qy, "qy")
+    m = qx.numel()
+    if qy.numel() != m:
+        raise ValueError("qx and qy must have the same length")
+    dt = torch.float64 if p.precision == AIDW_FP64_PLAIN else torch.float32
+    if out_z is None:
+        out_z = torch.full((m,), float("nan"), dtype=dt, device=qx.device)
+    if out_alpha is None and want_alpha:
+        out_alpha = torch.full((m,), float("nan"), dtype=dt, device=qx.device)
+    for t, name in ((out_z, "out_z"), (out_alpha, "out_alpha")):
+        if t is not None and (t.dtype != dt or t.numel() != m or not t.is_contiguous()):
+            raise TypeError(f"{name} must be a contiguous {dt} tensor of length {m}")
+    pc = p.to_c()
+    _check(load().aidw_interpolate_shard(grid.handle, _ptr(qx), _ptr(qy), m, int(shard),
+                                         int(n_shards), ctypes.byref(pc), _ptr(out_z),
+                                         _ptr(out_alpha), _stream(stream)),
+           "aidw_interpolate_shard")
+    return out_z, out_alpha
+
+
 def aidw_test_expire_next_wait(tries: int = 50) -> None:
     """Test hook: the next weighting launch's bounded wait expires after tries."""
     _check(load().aidw_test_expire_next_wait(int(tries)), "aidw_test_expire_next_wait")
@@ -361,6 +405,21 @@ def aidw_probe_pipe_rates() -> dict:
     r = [ctypes.c_double() for _ in range(3)]
     _check(load().aidw_probe_pipe_rates(*(ctypes.byref(v) for v in r)), "aidw_probe_pipe_rates")
     return {"lg2": r[0].value, "ex2": r[1].value, "ffma2_lanes": r[2].value}
+
+
+def aidw_weight_mix() -> dict:
+    """Instruction mix of the float32 weighting loop: products per inner
+    step, how many take exp2 / log2 from FMA-pipe polynomials, and the
+    FMA-pipe lane operations and other instructions per pair of the base
+    loop and of each polynomial (host only, no GPU needed)."""
+    prod, pe, pl = ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
+    lanes = (ctypes.c_double * 3)()
+    instr = (ctypes.c_double * 3)()
+    _check(load().aidw_weight_mix(ctypes.byref(prod), ctypes.byref(pe), ctypes.byref(pl), lanes,
+                                  instr), "aidw_weight_mix")
+    return {"products": prod.value, "poly_exp2": pe.value, "poly_lg2": pl.value,
+            "fma_lanes": {"base": lanes[0], "exp2_poly": lanes[1], "lg2_poly": lanes[2]},
+            "instr": {"base": instr[0], "exp2_poly": instr[1], "lg2_poly": instr[2]}}
 
 
 @dataclass

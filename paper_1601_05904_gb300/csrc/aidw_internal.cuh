@@ -177,6 +177,8 @@ aidw_status weight_launch_batch(const WJob *jobs, int n_jobs, long long total_u,
                                 long long total_q, bool fp64, void *part, long long G,
                                 int *status, int device, cudaStream_t s);
 size_t weight_partial_bytes(bool fp64);  // bytes of one query tile's partials
+// Instruction mix of the float32 weighting loop (see aidw_weight_mix).
+void weight_mix(int *products, int *poly_exp2, int *poly_lg2, double *fma_lanes, double *instr);
 // Test hook: the next weighting launch leaves one data-tile copy unissued and
 // bounds its waits at `tries` tries, so a wait expires.
 void weight_expire_next_wait(int tries);

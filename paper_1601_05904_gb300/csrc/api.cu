@@ -465,6 +465,38 @@ aidw_status aidw_interpolate_local(const aidw_grid *g, const float *qx, const fl
                       reinterpret_cast<cudaStream_t>(stream), out_z);
 }
 
+aidw_status aidw_shard_range(int64_t n_query, int shard, int n_shards, int64_t *begin,
+                             int64_t *end)
+{
+    if (!begin || !end || n_query < 0 || n_shards < 1 || shard < 0 || shard >= n_shards)
+        return AIDW_ERR_INVALID_ARG;
+    // the first n_query % n_shards shards take one query more
+    const int64_t q = n_query / n_shards, r = n_query % n_shards;
+    *begin = (int64_t)shard * q + (shard < r ? shard : r);
+    *end = *begin + q + (shard < r ? 1 : 0);
+    return AIDW_OK;
+}
+
+aidw_status aidw_interpolate_shard(const aidw_grid *g, const float *qx, const float *qy,
+                                   int64_t n_query, int shard, int n_shards,
+                                   const aidw_params *p, void *out_z, void *out_alpha,
+                                   aidw_stream_t stream)
+{
+    if (!g || n_query < 0 || n_query > kMaxPoints) return AIDW_ERR_INVALID_ARG;
+    int64_t b = 0, e = 0;
+    aidw_status st = aidw_shard_range(n_query, shard, n_shards, &b, &e);
+    if (st != AIDW_OK) return st;
+    st = check_params(p, true);
+    if (st != AIDW_OK) return st;
+    if (p->k > g->n_data) return AIDW_ERR_K_RANGE;
+    if (e == b) return AIDW_OK;
+    if (!qx || !qy || !out_z) return AIDW_ERR_INVALID_ARG;
+    const size_t es = p->precision == AIDW_FP64_PLAIN ? sizeof(double) : sizeof(float);
+    void *oz = static_cast<unsigned char *>(out_z) + es * (size_t)b;
+    void *oa = out_alpha ? static_cast<unsigned char *>(out_alpha) + es * (size_t)b : nullptr;
+    return aidw_interpolate(g, qx + b, qy + b, e - b, p, oz, oa, stream);
+}
+
 aidw_status aidw_set_memory_limit(int64_t bytes, int64_t *held)
 {
     if (bytes < 0) return AIDW_ERR_INVALID_ARG;

@@ -22,9 +22,11 @@
 // aidw_knn_paper_rule) to measure how often it misses a neighbour.
 //
 // After the search the thread computes r_obs (Eq. 3), R (Eq. 4), mu (Eq. 5)
-// and alpha (Eq. 6) in float64 and writes one record for the weighting
-// stage: alpha, the smallest squared distance and the mean z of data points
-// at distance 0 (the limit of Eq. 1 when the query coincides with data).
+// and alpha (Eq. 6) - in float64 on the float64 path; on the float32 path
+// r_obs as a compensated float32 sum of float32 square roots and Eq. 4-6 in
+// float32 - and writes one record for the weighting stage: alpha, the
+// smallest squared distance and the mean z of data points at distance 0
+// (the limit of Eq. 1 when the query coincides with data).
 #include <math.h>
 #include <stdlib.h>
 #include <string.h>

@@ -1,7 +1,10 @@
 // aidw_interpolate_noalloc: the AIDW prediction of aidw_interpolate with its
 // per-call scratch in a fixed array of the library's device image instead of
 // an allocation, for callers that cannot let the library allocate (see
-// include/aidw.h).  The kernels are the ones aidw_interpolate launches.
+// include/aidw.h).  The kNN and weighting kernels are the ones
+// aidw_interpolate launches; the query cell-ordering pass that
+// aidw_interpolate runs first (from 4096 queries) is left out, because its
+// temporaries would need an allocation.
 #include <mutex>
 
 #include "aidw_internal.cuh"
@@ -18,12 +21,20 @@ void *g_scratch_addr[kMaxDevices] = {};
 
 // Device address of the scratch array on `device` (the current device).  In
 // host code the array's name is only a host-side stand-in, so the address is
-// looked up once per device with cudaGetSymbolAddress.
-aidw_status scratch_address(int device, void **out)
+// looked up once per device with cudaGetSymbolAddress.  That look-up is host
+// set-up (it may load the library's device code), which must not happen
+// while `s` is being captured into a graph: such a first call is refused.
+aidw_status scratch_address(int device, cudaStream_t s, void **out)
 {
     if (device < 0 || device >= kMaxDevices) return AIDW_ERR_INVALID_ARG;
     std::lock_guard<std::mutex> lk(g_setup_mu);
     if (!g_scratch_addr[device]) {
+        cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+        if (cudaStreamIsCapturing(s, &cs) != cudaSuccess) {
+            cudaGetLastError();
+            return AIDW_ERR_CUDA;
+        }
+        if (cs != cudaStreamCaptureStatusNone) return AIDW_ERR_INVALID_ARG;
         void *p = nullptr;
         const cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
         if (e != cudaSuccess || !p) {
@@ -56,8 +67,9 @@ extern "C" aidw_status aidw_interpolate_noalloc(const aidw_grid *g, const float 
         return AIDW_ERR_CUDA;
     }
     if (device != g->device) return AIDW_ERR_INVALID_ARG;
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
     void *base = nullptr;
-    aidw_status st = scratch_address(device, &base);
+    aidw_status st = scratch_address(device, s, &base);
     if (st != AIDW_OK) return st;
 
     const size_t rec_bytes = (sizeof(QRec) * (size_t)n_query + 255) / 256 * 256;
@@ -65,8 +77,10 @@ extern "C" aidw_status aidw_interpolate_noalloc(const aidw_grid *g, const float 
     void *part = static_cast<unsigned char *>(base) + rec_bytes;
     const size_t part_bytes = (size_t)AIDW_NOALLOC_SCRATCH_BYTES - rec_bytes;
 
-    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
     const bool fp64 = p->precision == AIDW_FP64_PLAIN;
+    // sort = false: the pass that visits the queries in grid-cell order needs
+    // pool memory, so the kNN takes the queries in input order (same results,
+    // slower on clustered data)
     st = knn_launch(g, qx, qy, n_query, p->k, fp64, api_detail::alpha_params(p), recs, nullptr,
                     nullptr, nullptr, out_alpha, s, nullptr, false);
     if (st == AIDW_OK)

@@ -105,3 +105,10 @@ extern "C" aidw_status aidw_probe_pipe_rates(double *lg2_per_sm_clk, double *ex2
     if (ffma2_lanes_per_sm_clk) *ffma2_lanes_per_sm_clk = r2;
     return st;
 }
+
+extern "C" aidw_status aidw_weight_mix(int *products, int *poly_exp2, int *poly_lg2,
+                                       double *fma_lanes, double *instr)
+{
+    aidw::weight_mix(products, poly_exp2, poly_lg2, fma_lanes, instr);
+    return AIDW_OK;
+}

@@ -155,6 +155,35 @@ __device__ __forceinline__ int aos_count(long long n_pad, long long d)
     return (int)min((long long)kDTile, n_pad - d * kDTile);
 }
 
+// After an expired wait the partial sums of the query tiles this CTA had not
+// finished (the current one and the later ones of its share) are unknown, so
+// its slots for them are set to NaN: the finalize step then returns NaN for
+// exactly the queries whose sum is incomplete, instead of adding whatever an
+// earlier launch left in those slots.  Called by every thread of the CTA.
+__device__ __forceinline__ void nan_part(float4 &p)
+{
+    const float nan = __int_as_float(0x7fc00000);
+    p = make_float4(nan, nan, nan, nan);
+}
+__device__ __forceinline__ void nan_part(double2 &p)
+{
+    const double nan = __longlong_as_double(0x7ff8000000000000LL);
+    p = make_double2(nan, nan);
+}
+template <typename Part, int QTILE, int NT>
+__device__ void poison_rest(const SKArgs &a, Part *part, long long cta, long long u, long long u1)
+{
+    Part bad;
+    nan_part(bad);
+    while (u < u1) {
+        const WJob J = job_of_unit(a, u);
+        const long long t = (u - J.unit_base) / J.D;
+        const long long slot = J.tile_base + t + cta;
+        for (int i = threadIdx.x; i < QTILE; i += NT) part[slot * QTILE + i] = bad;
+        u = J.unit_base + (t + 1) * J.D;  // first unit of the next query tile
+    }
+}
+
 template <bool HOOK>
 __device__ __forceinline__ void issue_tile_soa(const SKArgs &a, float *buf, uint64_t *bar,
                                                long long u)
@@ -315,6 +344,7 @@ __global__ void __launch_bounds__(THREADS, MINB)
                         mbar_wait_bounded(&full[(v - u0) % kStages],
                                           (uint32_t)(((v - u0) / kStages) & 1), wait_tries);
                 __syncthreads();
+                poison_rest<float4, C::kQTile, THREADS>(a, part, cta, u, u1);
                 return;
             }
             if (threadIdx.x == 0 && u + kStages < u1)
@@ -439,6 +469,7 @@ __global__ void __launch_bounds__(WCfg<true>::kThreads, WCfg<true>::kMinBlocks)
                         mbar_wait_bounded(&full[(v - u0) % kStages],
                                           (uint32_t)(((v - u0) / kStages) & 1), wait_tries);
                 __syncthreads();
+                poison_rest<double2, C::kQTile, C::kThreads>(a, part, cta, u, u1);
                 return;
             }
             if (threadIdx.x == 0 && u + kStages < u1)
@@ -497,18 +528,33 @@ const PolySplit kPolySplits[] = {
     {4, 0, k_weight_f32<4, 0>}, {0, 1, k_weight_f32<0, 1>}, {1, 1, k_weight_f32<1, 1>},
     {0, 2, k_weight_f32<0, 2>}};
 constexpr int kNumPolySplits = (int)(sizeof(kPolySplits) / sizeof(kPolySplits[0]));
-F32Kernel f32_kernel()
+const PolySplit &f32_split()
 {
-    static const F32Kernel k = [] {
+    static const int idx = [] {
         const char *e = getenv("AIDW_WEIGHT_POLY");
         int pe = -1, pl = -1;
         if (e && sscanf(e, "%d,%d", &pe, &pl) == 2)
             for (int i = 0; i < kNumPolySplits; ++i)
-                if (kPolySplits[i].e == pe && kPolySplits[i].l == pl) return kPolySplits[i].kernel;
-        return kPolySplits[0].kernel;
+                if (kPolySplits[i].e == pe && kPolySplits[i].l == pl) return i;
+        return 0;
     }();
-    return k;
+    return kPolySplits[idx];
 }
+F32Kernel f32_kernel() { return f32_split().kernel; }
+
+// Work of the float32 loop per (query, data point) pair, counted from the
+// source above and from f2_exp2_poly / f2_log2_poly (aidw_device.cuh), for
+// roofline accounting.  FMA-pipe lane operations: the base loop takes 7 (two
+// differences, the squared distance as a multiply and an fma, the exponent
+// fma, the two sums); an exp2 polynomial 8 (three for the reduction, five
+// fmas); a log2 polynomial 10 (two for the reduction, eight fmas).
+// Instructions other than the SFU's own (a packed f32x2 instruction covers
+// two pairs): base 3.5; exp2 polynomial 7 (four packed, one fmax and two
+// integer exponent operations per lane); log2 polynomial 12 (five packed,
+// five integer operations and a compare-select per lane).  Loads, loop
+// control and the chunk folds (about 0.2 per pair) are not included.
+constexpr double kFmaLanes[3] = {7.0, 8.0, 10.0};
+constexpr double kInstr[3] = {3.5, 7.0, 12.0};
 
 // Dynamic shared memory of the weighting kernels: kStages data tiles.
 template <bool F64>
@@ -657,6 +703,18 @@ aidw_status run_scratch(const aidw_grid *g, const float *qx, const float *qy, lo
 }
 
 }  // namespace
+
+void weight_mix(int *products, int *poly_exp2, int *poly_lg2, double *fma_lanes, double *instr)
+{
+    const PolySplit &sp = f32_split();
+    if (products) *products = 2 * WCfg<false>::kQPT;
+    if (poly_exp2) *poly_exp2 = sp.e;
+    if (poly_lg2) *poly_lg2 = sp.l;
+    for (int i = 0; i < 3; ++i) {
+        if (fma_lanes) fma_lanes[i] = kFmaLanes[i];
+        if (instr) instr[i] = kInstr[i];
+    }
+}
 
 void weight_expire_next_wait(int tries)
 {

@@ -108,3 +108,35 @@ def test_binding_fails_loudly_without_library(tmp_path):
             binding.load(str(tmp_path / "nope.so"))
         finally:
             binding._lib = saved
+
+
+def test_weight_mix_is_host_only(lib):
+    """The weighting loop's instruction mix (roofline accounting) answers
+    without a GPU; the default split takes 2 of 8 exp2s from the FMA pipe."""
+    from paper_1601_05904_gb300 import binding
+    mix = binding.aidw_weight_mix()
+    assert mix["products"] == 8
+    assert (mix["poly_exp2"], mix["poly_lg2"]) == (2, 0)
+    assert mix["fma_lanes"] == {"base": 7.0, "exp2_poly": 8.0, "lg2_poly": 10.0}
+    assert mix["instr"]["base"] == 3.5
+
+
+@pytest.mark.parametrize("n,world", [(0, 1), (0, 3), (1, 4), (10, 3), (1 << 20, 8), (1000003, 7)])
+def test_shard_range_partitions_the_queries(lib, n, world):
+    """Shards are contiguous, in shard order, cover [0, n) exactly once and
+    differ in size by at most one (the rule of aidw_shard_range)."""
+    from paper_1601_05904_gb300 import binding
+    sl = [binding.aidw_shard_range(n, r, world) for r in range(world)]
+    assert sl[0][0] == 0 and sl[-1][1] == n
+    for (b0, e0), (b1, e1) in zip(sl, sl[1:]):
+        assert e0 == b1
+    sizes = [e - b for b, e in sl]
+    assert min(sizes) >= 0 and max(sizes) - min(sizes) <= 1
+    assert sizes == sorted(sizes, reverse=True)
+
+
+def test_shard_range_rejects_bad_shards(lib):
+    b, e = ctypes.c_int64(), ctypes.c_int64()
+    for n, r, w in ((-1, 0, 1), (10, 1, 1), (10, -1, 2), (10, 0, 0)):
+        assert lib.aidw_shard_range(n, r, w, ctypes.byref(b), ctypes.byref(e)) == 1
+    assert lib.aidw_shard_range(10, 0, 1, None, ctypes.byref(e)) == 1

@@ -1,6 +1,8 @@
-"""Host-side logic of the multi-GPU (query-sharded, weak-scaling) benchmark,
-run as two gloo ranks on CPU: every rank gets the same data points and its
-own queries, and the reported time is the slowest rank's."""
+"""Host-side logic of the multi-GPU paths, run as two gloo ranks on CPU:
+the query-sharded benchmark (every rank gets the same data points and its
+own queries, and the reported time is the slowest rank's), and the
+sharding of one query set (each rank computes its slice, the all-gathered
+slices equal the one-process result)."""
 import os
 import socket
 import sys
@@ -86,3 +88,54 @@ def test_reference_arm_under_torchrun_prints_one_line_from_rank_zero(tmp_path):
     import oracle
     if oracle.has_openmp():
         assert d["cpu_baseline"]["cores"] == len(os.sched_getaffinity(0))
+
+
+def _shard_rank(rank, world, port, out):
+    """One rank of a sharded interpolation with the oracle standing in for
+    the GPU: the slice comes from the library's aidw_shard_range (host
+    only), the gather is the package's gather_slices."""
+    sys.path.insert(0, ROOT)
+    import torch
+    import torch.distributed as dist
+
+    import oracle
+    from paper_1601_05904_gb300 import binding, inputs, shard
+    os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port))
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    try:
+        binding.load()
+        w = inputs.unit_square(n=1500, m=301, k=7, seed=5)
+        b, e = binding.aidw_shard_range(w.m, rank, world)
+        local = torch.full((w.m,), float("nan"), dtype=torch.float64)
+        if e > b:
+            local[b:e] = torch.from_numpy(
+                oracle.aidw(w.x, w.y, w.z, w.qx[b:e], w.qy[b:e], w.k, nthreads=1)["z"])
+        full = shard.gather_slices(local, w.m)
+        out.put((rank, (b, e), full.numpy()))
+    finally:
+        dist.destroy_process_group()
+
+
+@pytest.mark.parametrize("world", [2, 3])
+def test_sharded_queries_gather_to_the_one_process_result(world):
+    import multiprocessing as mp
+    oracle = pytest.importorskip("oracle")
+    from paper_1601_05904_gb300 import build, inputs
+    build.build()
+    oracle.build()
+    ctx = mp.get_context("spawn")
+    q = ctx.Queue()
+    port = _free_port()
+    ps = [ctx.Process(target=_shard_rank, args=(r, world, port, q)) for r in range(world)]
+    for p in ps:
+        p.start()
+    res = sorted(q.get(timeout=300) for _ in range(world))
+    for p in ps:
+        p.join(timeout=60)
+        assert p.exitcode == 0
+    w = inputs.unit_square(n=1500, m=301, k=7, seed=5)
+    ref = oracle.aidw(w.x, w.y, w.z, w.qx, w.qy, w.k, nthreads=1)["z"]
+    # the slices tile the query set, and every rank holds the whole result
+    assert [r[1] for r in res][0][0] == 0 and res[-1][1][1] == w.m
+    for rank, _, full in res:
+        np.testing.assert_array_equal(full, ref)
