@@ -149,7 +149,9 @@ aidw_status aidw_knn(const aidw_grid *g, const float *qx, const float *qy, int64
 /* AIDW prediction of every query: kNN (above), then per query r_exp
  * (Eq. 2), R (Eq. 4), mu (Eq. 5) and alpha (Eq. 6), then Eq. 1 summed over
  * ALL data points of the grid.  A query at distance 0 from data points
- * returns the mean z of those points (the limit of Eq. 1).
+ * returns the mean z of those points (the limit of Eq. 1).  If a bounded
+ * wait of the weighting stage expires (aidw_grid_status then reports
+ * AIDW_ERR_TIMEOUT), every prediction of the call is NaN.
  *  out_z      [n_query] predictions: float32 for AIDW_FP32_COMP, float64
  *             for AIDW_FP64_PLAIN
  *  out_alpha  [n_query] alpha of each query, same element type; or NULL
@@ -228,17 +230,41 @@ aidw_status aidw_batch_plan_create(const aidw_job *jobs, int n_jobs, const aidw_
  * stay valid and unchanged until the stream reaches the end of the run. */
 aidw_status aidw_batch_run(aidw_batch_plan *plan, const aidw_job *jobs, aidw_stream_t stream);
 
-/* Autotuner: runs the grid build and kNN of the plan for each candidate
- * cell-width scale (unless params->cell_scale fixed it) and kNN block size,
- * keeps the fastest and discards the captured graph.  Synchronous.
- * *best_ms (may be NULL) receives the best build+kNN time. */
+/* Jobs are grouped by top-k width class: the kNN of a job runs in the
+ * launch of the smallest class whose register slots (8, 16, 24, 32) hold
+ * its k.  Each class has its own cell-width scale (of its jobs' grids) and
+ * kNN block size; the defaults are the single-grid choices (scale 2 up to
+ * k = 16, 3 above; 128-thread blocks). */
+#define AIDW_BATCH_CLASSES 4
+
+/* Autotuner: times the grid build + kNN of all jobs (two runs per candidate,
+ * the second counted) and descends class by class: for every class with
+ * queries, the cell-width scales {1, 1.5, 2, 3, 4} (unless params->cell_scale
+ * fixed it), then the kNN block sizes {warp per query, 64, 128, 256},
+ * keeping whatever lowers the total.  Discards the captured graph.
+ * Synchronous.  *best_ms (may be NULL) receives the best build+kNN time.
+ * The result is cached in the process under a key of the precision, the
+ * GPU's SM count, a fixed scale and the histogram of the jobs' shapes (log2
+ * buckets of n_data and n_query, and k); aidw_batch_plan_create applies a
+ * cached tuning to a plan with the same key.  With the environment variable
+ * AIDW_TUNE_CACHE=<file> entries are also loaded from and appended to that
+ * file. */
 aidw_status aidw_batch_plan_tune(aidw_batch_plan *plan, const aidw_job *jobs,
                                  aidw_stream_t stream, double *best_ms);
 
-/* The plan's current choices and size: cell-width scale, kNN block size,
- * sum over jobs of n_data * n_query, pool bytes.  Any output may be NULL. */
+/* The plan's size and the choices of its largest class (by queries):
+ * cell-width scale, kNN block size (0: warp per query), sum over jobs of
+ * n_data * n_query, pool bytes.  Any output may be NULL. */
 aidw_status aidw_batch_plan_get(const aidw_batch_plan *plan, double *cell_scale,
                                 int *knn_threads, int64_t *total_pairs, int64_t *pool_bytes);
+
+/* Per class (arrays of AIDW_BATCH_CLASSES): register slots, cell-width
+ * scale, kNN block size and queries of the class; *source: 0 defaults,
+ * 1 measured by aidw_batch_plan_tune, 2 taken from the tuning cache when
+ * the plan was created.  Any output may be NULL.  Host only. */
+aidw_status aidw_batch_plan_get_classes(const aidw_batch_plan *plan, int *kmax,
+                                        double *cell_scale, int *knn_threads, int64_t *queries,
+                                        int *source);
 
 /* Synchronises the device and returns then clears the device-side errors of
  * the last runs (any job). */
@@ -275,8 +301,9 @@ aidw_status aidw_batch(const aidw_job *jobs, int n_jobs, const aidw_params *p,
  *    on a stream that is being captured returns AIDW_ERR_INVALID_ARG and
  *    enqueues nothing.
  *  - If a weighting wait expires (aidw_grid_status then reports
- *    AIDW_ERR_TIMEOUT), the queries whose sums were left incomplete get NaN
- *    predictions, as in aidw_interpolate.
+ *    AIDW_ERR_TIMEOUT), every prediction of that call is NaN, as in
+ *    aidw_interpolate: no sum left in the shared array by an earlier call
+ *    reaches the output.
  *  - Every call on a device shares the one array: calls that can overlap on
  *    the GPU (different streams, no ordering between them) race on it.
  *    Calls ordered on one stream are safe.  Nothing in the array needs to
@@ -337,11 +364,10 @@ aidw_status aidw_set_memory_limit(int64_t bytes, int64_t *held);
  * batch run; a launch being captured into a graph leaves the hook for the
  * next one) leaves the copy of one data tile unissued and bounds its waits
  * at `tries` (1..2000) tries, so the CTA that needs that tile gives up: it
- * latches AIDW_ERR_TIMEOUT, waits (bounded) for its own copies in flight,
- * marks the partial sums it had not finished as NaN and returns.  The GPU
- * stays usable; the queries whose sums that CTA had not finished get NaN
- * predictions, the others are computed normally; aidw_grid_status (or
- * aidw_batch_plan_status) reports the timeout. */
+ * latches AIDW_ERR_TIMEOUT, sets the launch's failure flag, waits (bounded)
+ * for its own copies in flight and returns.  The GPU stays usable; every
+ * prediction of that launch is NaN (the finalize step reads the flag);
+ * aidw_grid_status (or aidw_batch_plan_status) reports the timeout. */
 aidw_status aidw_test_expire_next_wait(int tries);
 
 /* Short English name of a status code (static storage). */
@@ -377,9 +403,9 @@ aidw_status aidw_probe_pipe_rates(double *lg2_per_sm_clk, double *ex2_per_sm_clk
 /* Instruction mix of the float32 weighting loop (AIDW_FP32_COMP) that this
  * library launches, for roofline accounting (no counterpart in the paper).
  * Every (query, data point) pair needs one log2 and one exp2; of every
- * *products pairs of the loop's inner step, *poly_exp2 take the exp2 and
- * *poly_lg2 the log2 from float32 polynomials on the FMA pipe instead of
- * the SFU.  fma_lanes[3] receives the FMA-pipe lane operations per pair of
+ * *products pairs of two consecutive inner steps of the loop, *poly_exp2
+ * take the exp2 and *poly_lg2 the log2 from float32 polynomials on the FMA
+ * pipe instead of the SFU.  fma_lanes[3] receives the FMA-pipe lane operations per pair of
  * the base loop, of one exp2 polynomial and of one log2 polynomial;
  * instr[3] the instructions per pair of the same three parts, not counting
  * the SFU instructions, loads and loop control (a packed two-lane

@@ -150,6 +150,9 @@ def load(path: str | None = None):
         lib.aidw_batch_plan_tune.argtypes = [vp, P(CJob), vp, P(ctypes.c_double)]
         lib.aidw_batch_plan_get.restype = c_int
         lib.aidw_batch_plan_get.argtypes = [vp, P(ctypes.c_double), P(c_int), P(i64), P(i64)]
+        lib.aidw_batch_plan_get_classes.restype = c_int
+        lib.aidw_batch_plan_get_classes.argtypes = [vp, P(c_int), P(ctypes.c_double), P(c_int),
+                                                    P(i64), P(c_int)]
         lib.aidw_batch_plan_status.restype = c_int
         lib.aidw_batch_plan_status.argtypes = [vp]
         lib.aidw_batch_plan_destroy.restype = c_int
@@ -509,6 +512,24 @@ def aidw_batch_plan_get(plan: BatchPlan) -> dict:
            "aidw_batch_plan_get")
     return {"cell_scale": cs.value, "knn_threads": th.value, "total_pairs": pairs.value,
             "pool_bytes": pool.value}
+
+
+BATCH_CLASSES = 4
+
+
+def aidw_batch_plan_get_classes(plan: BatchPlan) -> dict:
+    """Per top-k class: slots, cell scale, kNN block size (0: warp per
+    query), queries; and where the choices came from (defaults / tuner /
+    cache)."""
+    n = BATCH_CLASSES
+    kmax, th = (ctypes.c_int * n)(), (ctypes.c_int * n)()
+    sc, q = (ctypes.c_double * n)(), (ctypes.c_int64 * n)()
+    src = ctypes.c_int()
+    _check(load().aidw_batch_plan_get_classes(plan.handle, kmax, sc, th, q, ctypes.byref(src)),
+           "aidw_batch_plan_get_classes")
+    return {"classes": [{"kmax": kmax[c], "cell_scale": sc[c], "knn_threads": th[c],
+                         "queries": q[c]} for c in range(n)],
+            "source": ("defaults", "tuner", "cache")[src.value]}
 
 
 def aidw_batch_plan_status(plan: BatchPlan) -> int:

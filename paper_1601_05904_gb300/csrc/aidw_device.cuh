@@ -125,9 +125,10 @@ __device__ __forceinline__ void f2_comp_add(F2 &hi, F2 &lo, F2 x)
 // (adding 1.5 * 2^23 rounds t to an integer in the low mantissa bits) and
 // f = t - n in [-1/2, 1/2] (exact: t and n are within a factor of two, or
 // n = 0); 2^f by a degree-5 polynomial fitted to minimise the relative error
-// on [-1/2, 1/2] (Lawson-iterated weighted least squares; max relative
-// error 7.5e-8, about 2e-7 after float32 rounding, comparable to
-// ex2.approx); 2^n applied by adding n to the exponent field.  t is clamped
+// on [-1/2, 1/2] (Lawson-iterated weighted least squares, generated by
+// fit_poly.py; max relative error 7.5e-8, 1.5e-7 with the coefficients
+// rounded to float32, comparable to ex2.approx); 2^n applied by adding n to
+// the exponent field.  t is clamped
 // below at -125 so the exponent cannot wrap; weights that small are below
 // 2^-124 of the largest weight (1) and vanish in the sums.
 __device__ __forceinline__ F2 f2_exp2_poly(F2 t)
@@ -138,12 +139,12 @@ __device__ __forceinline__ F2 f2_exp2_poly(F2 t)
     const F2 magic = f2_pack(12582912.0f, 12582912.0f);  // 1.5 * 2^23
     const F2 r = f2_add(tc, magic);
     const F2 f = f2_sub(tc, f2_sub(r, magic));
-    F2 p = f2_fma(f2_pack(1.327647129073739e-03f, 1.327647129073739e-03f), f,
-                  f2_pack(9.675541892647743e-03f, 9.675541892647743e-03f));
-    p = f2_fma(p, f, f2_pack(5.550713092088699e-02f, 5.550713092088699e-02f));
-    p = f2_fma(p, f, f2_pack(2.402212023735046e-01f, 2.402212023735046e-01f));
-    p = f2_fma(p, f, f2_pack(6.931469440460205e-01f, 6.931469440460205e-01f));
-    p = f2_fma(p, f, f2_pack(1.000000119209290e+00f, 1.000000119209290e+00f));
+    F2 p = f2_fma(f2_pack(1.3276444515213370e-03f, 1.3276444515213370e-03f), f,
+                  f2_pack(9.6755353733897209e-03f, 9.6755353733897209e-03f));
+    p = f2_fma(p, f, f2_pack(5.5507134646177292e-02f, 5.5507134646177292e-02f));
+    p = f2_fma(p, f, f2_pack(2.4022120237350464e-01f, 2.4022120237350464e-01f));
+    p = f2_fma(p, f, f2_pack(6.9314694404602051e-01f, 6.9314694404602051e-01f));
+    p = f2_fma(p, f, f2_pack(1.0000001192092896e+00f, 1.0000001192092896e+00f));
     float r0, r1, p0, p1;
     f2_unpack(r, r0, r1);
     f2_unpack(p, p0, p1);
@@ -159,9 +160,10 @@ __device__ __forceinline__ F2 f2_exp2_poly(F2 t)
 // has the bits (i & 0x7FFFFF) + bits(sqrt(1/2)), so both come from integer
 // operations; e becomes a float by the 1.5 * 2^23 exponent-field trick.  With
 // s = m - 1 in [-0.293, 0.415), log2(1 + s) = s * P(s), P of degree 7 fitted
-// to minimise the absolute error (Lawson-iterated weighted least squares;
-// 4.8e-8 before rounding, 1.0e-7 when evaluated in float32 on [1/2, 2],
-// inside the 2^-22.6 bound of lg2.approx).  +inf maps to +inf, so padding
+// to minimise the absolute error (Lawson-iterated weighted least squares,
+// generated by fit_poly.py; 4.8e-8 before rounding, about 1e-7 when
+// evaluated in float32 on [1/2, 2], inside the 2^-22.6 bound of
+// lg2.approx).  +inf maps to +inf, so padding
 // points keep weight 0; x = 0 gives -127 (zero distances are never weighted:
 // such queries are replaced in the finalize step).
 __device__ __forceinline__ F2 f2_log2_poly(F2 x)
@@ -177,13 +179,13 @@ __device__ __forceinline__ F2 f2_log2_poly(F2 x)
                                 __int_as_float((i1 >> 23) + 0x4B400000)),
                         magic);
     const F2 s = f2_sub(m, f2_pack(1.0f, 1.0f));
-    F2 p = f2_fma(f2_pack(-1.4574451744556427e-01f, -1.4574451744556427e-01f), s,
-                  f2_pack(2.3689043521881104e-01f, 2.3689043521881104e-01f));
-    p = f2_fma(p, s, f2_pack(-2.500690519809723e-01f, -2.500690519809723e-01f));
-    p = f2_fma(p, s, f2_pack(2.8670746088027954e-01f, 2.8670746088027954e-01f));
-    p = f2_fma(p, s, f2_pack(-3.6008721590042114e-01f, -3.6008721590042114e-01f));
+    F2 p = f2_fma(f2_pack(-1.4574408531188965e-01f, -1.4574408531188965e-01f), s,
+                  f2_pack(2.3688933253288269e-01f, 2.3688933253288269e-01f));
+    p = f2_fma(p, s, f2_pack(-2.5006875395774841e-01f, -2.5006875395774841e-01f));
+    p = f2_fma(p, s, f2_pack(2.8670758008956909e-01f, 2.8670758008956909e-01f));
+    p = f2_fma(p, s, f2_pack(-3.6008724570274353e-01f, -3.6008724570274353e-01f));
     p = f2_fma(p, s, f2_pack(4.8093944787979126e-01f, 4.8093944787979126e-01f));
-    p = f2_fma(p, s, f2_pack(-7.213571667671204e-01f, -7.213571667671204e-01f));
+    p = f2_fma(p, s, f2_pack(-7.2135716676712036e-01f, -7.2135716676712036e-01f));
     p = f2_fma(p, s, f2_pack(1.4426947832107544e+00f, 1.4426947832107544e+00f));
     float l0, l1;
     f2_unpack(f2_fma(s, p, e), l0, l1);

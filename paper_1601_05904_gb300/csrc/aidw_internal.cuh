@@ -60,7 +60,8 @@ struct QRec {
 struct aidw_grid {
     aidw::GridDev *dev;          // device struct
     aidw::Point *pts;            // [n_pad] cell-ordered points, padded
-    int *cell_start;             // [cap + 1] head of each cell (int32)
+    int *cell_start;             // [cap + 1] head of each cell (int32), then the
+                                 // build's scan records (grid_cell_start_ints)
     int *perm;                   // [n_data] original index at each position
     float *wt;                   // [n_wtiles][3][kWeightTile] weighting tiles
     float *zorig;                // [n_data] z in the caller's order (local AIDW)
@@ -89,6 +90,9 @@ void profile_end(int handle, cudaStream_t s, int stage, int launches);
 
 // ---- stages (defined in grid_build.cu, knn.cu, weight.cu) ------------------
 long long grid_cells_capacity(long long n, double c);
+// Ints to allocate for a grid's cell_start array of capacity cap (the cell
+// heads plus the build's scan records and tickets).
+long long grid_cell_start_ints(long long cap);
 aidw_status grid_build_launch(aidw_grid *g, const float *x, const float *y, const float *z,
                               cudaStream_t s);
 
@@ -157,7 +161,7 @@ aidw_status knn_launch_brute(const aidw_grid *g, const float *qx, const float *q
                              float *out_robs, cudaStream_t s);
 
 // Batched kNN over jobs[0, n_jobs) (device array) whose k all need at most
-// kmax (8, 16 or 32) slots; total_q is the sum of their query counts.
+// kmax (8, 16, 24 or 32) slots; total_q is the sum of their query counts.
 // threads: block size of the thread-per-query kernel, or 0 for the
 // warp-per-query kernel.
 int knn_default_threads(int k);
@@ -172,10 +176,12 @@ int weight_resident_ctas(int device, bool fp64);
 
 // Batched weighting + finalize over jobs[0, n_jobs) (device array), total_u
 // units and total_q queries; part holds (total tiles + G) * query-tile
-// partial records.
+// partial records; fail is one int of device memory for the launch's
+// failure flag (zeroed by the launch; a CTA whose wait expires sets it and
+// the finalize then writes NaN).
 aidw_status weight_launch_batch(const WJob *jobs, int n_jobs, long long total_u,
                                 long long total_q, bool fp64, void *part, long long G,
-                                int *status, int device, cudaStream_t s);
+                                int *status, int *fail, int device, cudaStream_t s);
 size_t weight_partial_bytes(bool fp64);  // bytes of one query tile's partials
 // Instruction mix of the float32 weighting loop (see aidw_weight_mix).
 void weight_mix(int *products, int *poly_exp2, int *poly_lg2, double *fma_lanes, double *instr);
@@ -189,9 +195,10 @@ aidw_status weight_launch(const aidw_grid *g, const float *qx, const float *qy,
                           long long n_query, bool fp64, const QRec *recs, void *out_z,
                           cudaStream_t s);
 
-// Same computation as weight_launch, with the partial sums in caller-given
-// device memory (scratch_bytes long) instead of an allocation; the number of
-// persistent CTAs is reduced if needed so that the partials fit.  Returns
+// Same computation as weight_launch, with the partial sums and the launch's
+// failure flag (the last 256 bytes) in caller-given device memory
+// (scratch_bytes long) instead of an allocation; the number of persistent
+// CTAs is reduced if needed so that the partials fit.  Returns
 // AIDW_ERR_INVALID_ARG if not even one CTA's partials fit.
 aidw_status weight_launch_scratch(const aidw_grid *g, const float *qx, const float *qy,
                                   long long n_query, bool fp64, const QRec *recs, void *out_z,

@@ -284,7 +284,8 @@ aidw_status aidw_grid_build(const float *x, const float *y, const float *z, int6
     cudaError_t e = lib_alloc((void **)&g->dev, sizeof(GridDev), s);
     if (e == cudaSuccess) e = lib_alloc((void **)&g->pts, sizeof(Point) * (size_t)g->n_pad, s);
     if (e == cudaSuccess)
-        e = lib_alloc((void **)&g->cell_start, sizeof(int) * (size_t)(g->cap_cells + 1), s);
+        e = lib_alloc((void **)&g->cell_start, sizeof(int) * (size_t)grid_cell_start_ints(g->cap_cells),
+                      s);
     if (e == cudaSuccess) e = lib_alloc((void **)&g->perm, sizeof(int) * (size_t)n_data, s);
     g->n_wtiles = (n_data + kWeightTile - 1) / kWeightTile;
     if (e == cudaSuccess)
@@ -305,6 +306,7 @@ aidw_status aidw_grid_build(const float *x, const float *y, const float *z, int6
         const int status = g->host_copy.status;
         if (st == AIDW_OK && (status & kStatusNonfiniteData)) st = AIDW_ERR_NONFINITE;
         if (st == AIDW_OK && (status & kStatusCapacity)) st = AIDW_ERR_INVALID_ARG;
+        if (st == AIDW_OK && (status & kStatusTimeout)) st = AIDW_ERR_TIMEOUT;
     }
     if (st != AIDW_OK) {
         aidw_grid_destroy(g);

@@ -13,9 +13,17 @@
 // and the kNN block size can be chosen by a measuring autotuner.
 #include <string.h>
 
+#include <math.h>
+#include <stdlib.h>
+
 #include <algorithm>
+#include <fstream>
+#include <map>
 #include <mutex>
 #include <new>
+#include <sstream>
+#include <string>
+#include <tuple>
 #include <vector>
 
 #include "aidw_device.cuh"
@@ -190,6 +198,17 @@ constexpr double kTuneScales[] = {1.0, 1.5, 2.0, 3.0, 4.0};
 constexpr int kTuneThreads[] = {0, 64, 128, 256};  // 0: warp per query
 constexpr double kMinScale = 1.0;
 
+// Top-k width classes: a job's kNN runs in the launch of the smallest class
+// whose register slots hold its k.
+constexpr int kClasses = AIDW_BATCH_CLASSES;
+constexpr int kClassKmax[kClasses] = {8, 16, 24, 32};
+inline int class_of(int k)
+{
+    for (int c = 0; c < kClasses; ++c)
+        if (k <= kClassKmax[c]) return c;
+    return kClasses - 1;
+}
+
 inline size_t align256(size_t b) { return (b + 255) / 256 * 256; }
 inline long long cdiv(long long a, long long b) { return (a + b - 1) / b; }
 
@@ -205,18 +224,20 @@ struct aidw_batch_plan {
     bool tuned_scale = false;   // cell scale chosen by the caller
     aidw_params params;
     AlphaParams ap;
-    double cell_scale = 1.0;
-    int knn_threads = 128;
+    // per top-k class: cell-width scale of its jobs' grids and kNN block size
+    double class_scale[kClasses] = {};
+    int class_threads[kClasses] = {};
+    int tuned = 0;  // 0: defaults, 1: measured by the tuner, 2: from the tuning cache
     std::vector<long long> n, m;
-    std::vector<int> k;
+    std::vector<int> k, jclass;
 
     // per-job layout (host copies of the device tables without caller pointers)
     std::vector<BJob> bj;
     std::vector<KnnJob> kj;   // ordered by top-k class
     std::vector<WJob> wj;
     std::vector<int> korder;  // job index of each kj entry
-    int kclass_begin[4] = {0, 0, 0, 0};
-    long long kclass_q[3] = {0, 0, 0};
+    int kclass_begin[kClasses + 1] = {};
+    long long kclass_q[kClasses] = {};
     long long total_pt_blocks = 0, total_bbox_blocks = 0, total_chunks = 0, total_pad_blocks = 0;
     long long total_q_blocks = 0;
     int *qcount_pool = nullptr;
@@ -240,6 +261,11 @@ struct aidw_batch_plan {
 
     cudaStream_t cap_stream = nullptr;
     cudaGraphExec_t exec = nullptr;
+    // the kNN launches of the classes run as parallel branches (side streams
+    // forked from and joined back to the launching stream)
+    cudaStream_t side[kClasses] = {};
+    cudaEvent_t fork = nullptr;
+    cudaEvent_t join[kClasses] = {};
 };
 
 namespace {
@@ -250,8 +276,8 @@ void layout_cells(aidw_batch_plan *P)
     long long blk_scan = 0;
     for (int j = 0; j < P->n_jobs; ++j) {
         BJob &b = P->bj[j];
-        b.cell_scale = P->cell_scale;
-        b.cap = grid_cells_capacity(b.n, P->cell_scale);
+        b.cell_scale = P->class_scale[P->jclass[j]];
+        b.cap = grid_cells_capacity(b.n, b.cell_scale);
         b.nchunks = cdiv(b.cap + 1, kScanChunk);
         b.blk_scan = blk_scan;
         blk_scan += b.nchunks;
@@ -322,16 +348,37 @@ aidw_status enqueue(aidw_batch_plan *P, cudaStream_t s, bool knn_only)
         k_b_qscatter<<<(unsigned)P->total_q_blocks, kThreads, 0, s>>>(P->d_bj, J);
     }
     aidw_status st = cuda_status(cudaGetLastError());
-    const int kmax_of_class[3] = {8, 16, 32};
-    for (int c = 0; c < 3 && st == AIDW_OK; ++c) {
+    // one kNN launch per class; the classes are independent, so all but the
+    // first with queries run on side streams forked from s after the build
+    // and joined back before the weighting: the launches overlap and fill
+    // each other's tails
+    bool forked = false;
+    int first = -1;
+    for (int c = 0; c < kClasses && st == AIDW_OK; ++c) {
         const int b = P->kclass_begin[c], e = P->kclass_begin[c + 1];
-        if (e > b)
-            st = knn_launch_batch(P->d_kj + b, e - b, P->kclass_q[c], kmax_of_class[c], P->fp64,
-                                  P->ap, P->knn_threads, s);
+        if (e == b) continue;
+        cudaStream_t cs = s;
+        if (first < 0) {
+            first = c;
+        } else {
+            if (!forked) {
+                st = cuda_status(cudaEventRecord(P->fork, s));
+                forked = true;
+            }
+            if (st == AIDW_OK) st = cuda_status(cudaStreamWaitEvent(P->side[c], P->fork, 0));
+            cs = P->side[c];
+        }
+        if (st == AIDW_OK)
+            st = knn_launch_batch(P->d_kj + b, e - b, P->kclass_q[c], kClassKmax[c], P->fp64,
+                                  P->ap, P->class_threads[c], cs);
+        if (st == AIDW_OK && cs != s) {
+            st = cuda_status(cudaEventRecord(P->join[c], cs));
+            if (st == AIDW_OK) st = cuda_status(cudaStreamWaitEvent(s, P->join[c], 0));
+        }
     }
     if (st != AIDW_OK || knn_only) return st;
     st = weight_launch_batch(P->d_wj, J, P->total_u, P->total_q, P->fp64, P->d_part, P->G,
-                             P->d_status, P->device, s);
+                             P->d_status, P->d_status + 1, P->device, s);
     if (st != AIDW_OK) return st;
     k_b_status<<<jb, 128, 0, s>>>(P->d_bj, J, P->d_status);
     return cuda_status(cudaGetLastError());
@@ -371,11 +418,107 @@ aidw_status check_jobs(const aidw_batch_plan *P, const aidw_job *jobs, int n_job
     return AIDW_OK;
 }
 
+// ---- tuning cache ---------------------------------------------------------------
+// The tuner's choices are kept per process, keyed by what they depend on: the
+// precision, the GPU's SM count, a cell scale fixed by the caller, and the
+// histogram of the jobs' shapes (log2 buckets of n and m, and k).  A plan
+// created for jobs with a cached key starts with that tuning.  With
+// AIDW_TUNE_CACHE=<file> the entries are also read from and appended to that
+// file (one line per entry: key, tab, the per-class scales and block sizes
+// and the measured build + kNN milliseconds), so later processes reuse them.
+struct TuneVal {
+    double scale[kClasses];
+    int threads[kClasses];
+    double ms;
+};
+std::mutex g_cache_mu;
+std::map<std::string, TuneVal> g_cache;
+bool g_cache_loaded = false;
+
+std::string tune_key(const aidw_batch_plan *P)
+{
+    int sms = 0;
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, P->device);
+    std::map<std::tuple<int, int, int>, int> hist;
+    for (int j = 0; j < P->n_jobs; ++j) {
+        const int bn = (int)ceil(log2((double)P->n[j]));
+        const int bm = P->m[j] > 0 ? (int)ceil(log2((double)P->m[j])) : -1;
+        ++hist[std::make_tuple(bn, bm, P->k[j])];
+    }
+    std::string key = "v1 fp64=" + std::to_string(P->fp64 ? 1 : 0) + " sms=" + std::to_string(sms) +
+                      " scale=" + std::to_string(P->tuned_scale ? P->params.cell_scale : 0.0);
+    for (const auto &h : hist)
+        key += " " + std::to_string(std::get<0>(h.first)) + "/" + std::to_string(std::get<1>(h.first)) +
+               "/" + std::to_string(std::get<2>(h.first)) + "x" + std::to_string(h.second);
+    return key;
+}
+
+void cache_load_file()
+{
+    if (g_cache_loaded) return;
+    g_cache_loaded = true;
+    const char *path = getenv("AIDW_TUNE_CACHE");
+    if (!path || !*path) return;
+    std::ifstream f(path);
+    std::string line;
+    while (std::getline(f, line)) {
+        const size_t tab = line.find('\t');
+        if (tab == std::string::npos) continue;
+        std::istringstream in(line.substr(tab + 1));
+        TuneVal v;
+        bool ok = true;
+        for (int c = 0; c < kClasses; ++c) ok = ok && (in >> v.scale[c]);
+        for (int c = 0; c < kClasses; ++c) ok = ok && (in >> v.threads[c]);
+        ok = ok && (in >> v.ms);
+        if (ok) g_cache[line.substr(0, tab)] = v;
+    }
+}
+
+bool cache_lookup(aidw_batch_plan *P)
+{
+    const std::string key = tune_key(P);
+    std::lock_guard<std::mutex> lk(g_cache_mu);
+    cache_load_file();
+    const auto it = g_cache.find(key);
+    if (it == g_cache.end()) return false;
+    for (int c = 0; c < kClasses; ++c) {
+        P->class_scale[c] = it->second.scale[c];
+        P->class_threads[c] = it->second.threads[c];
+    }
+    return true;
+}
+
+void cache_store(const aidw_batch_plan *P, double ms)
+{
+    const std::string key = tune_key(P);
+    TuneVal v;
+    for (int c = 0; c < kClasses; ++c) {
+        v.scale[c] = P->class_scale[c];
+        v.threads[c] = P->class_threads[c];
+    }
+    v.ms = ms;
+    std::lock_guard<std::mutex> lk(g_cache_mu);
+    cache_load_file();
+    g_cache[key] = v;
+    const char *path = getenv("AIDW_TUNE_CACHE");
+    if (!path || !*path) return;
+    std::ofstream f(path, std::ios::app);
+    f << key << '\t';
+    for (int c = 0; c < kClasses; ++c) f << v.scale[c] << ' ';
+    for (int c = 0; c < kClasses; ++c) f << v.threads[c] << ' ';
+    f << v.ms << '\n';
+}
+
 void free_plan(aidw_batch_plan *P)
 {
     if (!P) return;
     if (P->exec) cudaGraphExecDestroy(P->exec);
     if (P->cap_stream) cudaStreamDestroy(P->cap_stream);
+    for (int c = 0; c < kClasses; ++c) {
+        if (P->side[c]) cudaStreamDestroy(P->side[c]);
+        if (P->join[c]) cudaEventDestroy(P->join[c]);
+    }
+    if (P->fork) cudaEventDestroy(P->fork);
     if (P->stage_done) cudaEventDestroy(P->stage_done);
     if (P->h_stage) cudaFreeHost(P->h_stage);
     if (P->pool) cudaFree(P->pool);
@@ -407,17 +550,24 @@ aidw_status aidw_batch_plan_create(const aidw_job *jobs, int n_jobs, const aidw_
     P->ap = api_detail::alpha_params(p);
     P->fp64 = p->precision == AIDW_FP64_PLAIN;
     P->tuned_scale = p->cell_scale > 0.0;
-    P->cell_scale = p->cell_scale > 0.0 ? p->cell_scale : 2.0;  // the tuner may change it
+    // defaults as the single-grid path (scale 2 up to k = 16, 3 above); the
+    // tuner may change them
+    for (int c = 0; c < kClasses; ++c) {
+        P->class_scale[c] = p->cell_scale > 0.0 ? p->cell_scale : (kClassKmax[c] <= 16 ? 2.0 : 3.0);
+        P->class_threads[c] = knn_default_threads(kClassKmax[c]);
+    }
     cudaGetDevice(&P->device);
     P->n.resize(n_jobs);
     P->m.resize(n_jobs);
     P->k.resize(n_jobs);
+    P->jclass.resize(n_jobs);
     P->bj.assign(n_jobs, BJob());
     P->wj.assign(n_jobs, WJob());
     for (int j = 0; j < n_jobs; ++j) {
         P->n[j] = jobs[j].n_data;
         P->m[j] = jobs[j].n_query;
         P->k[j] = jobs[j].k > 0 ? jobs[j].k : p->k;
+        P->jclass[j] = class_of(P->k[j]);
     }
 
     // ---- sizes and block prefixes ----
@@ -430,7 +580,7 @@ aidw_status aidw_batch_plan_create(const aidw_job *jobs, int n_jobs, const aidw_
         return o;
     };
     // the start region is sized for the smallest scale the tuner may pick
-    const double scale_for_cap = P->tuned_scale ? P->cell_scale : std::min(kMinScale, P->cell_scale);
+    const double scale_for_cap = P->tuned_scale ? p->cell_scale : kMinScale;
     std::vector<size_t> o_pts(n_jobs), o_wt(n_jobs), o_start(n_jobs), o_perm(n_jobs),
         o_key(n_jobs), o_rank(n_jobs), o_tmp(n_jobs), o_bsum(n_jobs), o_rec(n_jobs),
         o_qkey(n_jobs), o_qrank(n_jobs), o_qorder(n_jobs);
@@ -500,7 +650,7 @@ aidw_status aidw_batch_plan_create(const aidw_job *jobs, int n_jobs, const aidw_
     const size_t o_qcountreg = take(sizeof(int) * (size_t)start_ints);
     const size_t o_part = take(weight_partial_bytes(P->fp64) * (size_t)(P->total_tiles + P->G));
     const size_t o_tables = take((sizeof(BJob) + sizeof(KnnJob) + sizeof(WJob)) * (size_t)n_jobs);
-    const size_t o_status = take(sizeof(int));
+    const size_t o_status = take(2 * sizeof(int));  // latched status, launch failure flag
     P->pool_bytes = off;
 
     cudaError_t e = cudaMalloc((void **)&P->pool, P->pool_bytes);
@@ -508,6 +658,11 @@ aidw_status aidw_batch_plan_create(const aidw_job *jobs, int n_jobs, const aidw_
                                              (sizeof(BJob) + sizeof(KnnJob) + sizeof(WJob)) * (size_t)n_jobs);
     if (e == cudaSuccess) e = cudaEventCreateWithFlags(&P->stage_done, cudaEventDisableTiming);
     if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&P->cap_stream, cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&P->fork, cudaEventDisableTiming);
+    for (int c = 0; c < kClasses && e == cudaSuccess; ++c) {
+        e = cudaStreamCreateWithFlags(&P->side[c], cudaStreamNonBlocking);
+        if (e == cudaSuccess) e = cudaEventCreateWithFlags(&P->join[c], cudaEventDisableTiming);
+    }
     if (e != cudaSuccess) {
         cudaGetLastError();
         free_plan(P);
@@ -545,16 +700,14 @@ aidw_status aidw_batch_plan_create(const aidw_job *jobs, int n_jobs, const aidw_
     }
     layout_cells(P);
 
-    // kNN table ordered by top-k class (8, 16, 32 slots)
+    // kNN table ordered by top-k class (8, 16, 24, 32 slots)
     P->korder.clear();
     P->kj.clear();
-    for (int c = 0; c < 3; ++c) {
+    for (int c = 0; c < kClasses; ++c) {
         P->kclass_begin[c] = (int)P->korder.size();
         long long qb = 0;
         for (int j = 0; j < n_jobs; ++j) {
-            const int k = P->k[j];
-            const int cls = k <= 8 ? 0 : (k <= 16 ? 1 : 2);
-            if (cls != c || P->m[j] == 0) continue;
+            if (P->jclass[j] != c || P->m[j] == 0) continue;
             KnnJob kj;
             memset(&kj, 0, sizeof(kj));
             kj.g = P->bj[j].g;
@@ -564,20 +717,25 @@ aidw_status aidw_batch_plan_create(const aidw_job *jobs, int n_jobs, const aidw_
             kj.order = P->bj[j].qorder;
             kj.nq = P->m[j];
             kj.q_base = qb;
-            kj.k = k;
+            kj.k = P->k[j];
             qb += P->m[j];
             P->kj.push_back(kj);
             P->korder.push_back(j);
         }
         P->kclass_q[c] = qb;
     }
-    P->kclass_begin[3] = (int)P->korder.size();
+    P->kclass_begin[kClasses] = (int)P->korder.size();
     // jobs without queries still need a kNN table slot for the upload layout
     while ((int)P->kj.size() < n_jobs) {
         KnnJob kj;
         memset(&kj, 0, sizeof(kj));
         P->kj.push_back(kj);
         P->korder.push_back(0);
+    }
+    // a tuning measured earlier for jobs of the same shapes
+    if (cache_lookup(P)) {
+        P->tuned = 2;
+        layout_cells(P);
     }
     // warm the weighting kernel's attributes before any capture
     weight_resident_ctas(P->device, P->fp64);
@@ -613,39 +771,76 @@ aidw_status aidw_batch_plan_tune(aidw_batch_plan *plan, const aidw_job *jobs,
     cudaEvent_t a = nullptr, b = nullptr;
     cudaEventCreate(&a);
     cudaEventCreate(&b);
-    const double old_scale = plan->cell_scale;
-    const int old_threads = plan->knn_threads;
-    double best = 1e30, best_scale = old_scale;
-    int best_threads = old_threads;
-    for (double sc : kTuneScales) {
-        if (plan->tuned_scale && sc != plan->params.cell_scale) continue;
-        plan->cell_scale = plan->tuned_scale ? plan->params.cell_scale : sc;
+    double old_scale[kClasses];
+    int old_threads[kClasses];
+    for (int c = 0; c < kClasses; ++c) {
+        old_scale[c] = plan->class_scale[c];
+        old_threads[c] = plan->class_threads[c];
+    }
+    // grid build + kNN of all jobs with the current choices (second of two runs)
+    auto measure = [&](double *ms_out) -> aidw_status {
         layout_cells(plan);
-        for (int th : kTuneThreads) {
-            plan->knn_threads = th;
-            st = upload_tables(plan, jobs, s);
-            if (st != AIDW_OK) break;
-            float ms = 0.0f;
-            for (int rep = 0; rep < 2 && st == AIDW_OK; ++rep) {
-                cudaEventRecord(a, s);
-                st = enqueue(plan, s, true);
-                cudaEventRecord(b, s);
-                if (cudaEventSynchronize(b) != cudaSuccess) st = AIDW_ERR_CUDA;
-                cudaEventElapsedTime(&ms, a, b);
+        aidw_status r = upload_tables(plan, jobs, s);
+        float ms = 0.0f;
+        for (int rep = 0; rep < 2 && r == AIDW_OK; ++rep) {
+            cudaEventRecord(a, s);
+            r = enqueue(plan, s, true);
+            cudaEventRecord(b, s);
+            if (cudaEventSynchronize(b) != cudaSuccess) r = AIDW_ERR_CUDA;
+            cudaEventElapsedTime(&ms, a, b);
+        }
+        *ms_out = ms;
+        return r;
+    };
+    // coordinate descent over the top-k classes: for each class that has
+    // queries, the cell scale of its jobs' grids (unless the caller fixed
+    // it), then the kNN block size, keeping whatever lowers the total
+    double best = 0.0;
+    st = measure(&best);
+    for (int c = 0; c < kClasses && st == AIDW_OK; ++c) {
+        if (plan->kclass_begin[c + 1] == plan->kclass_begin[c]) continue;
+        if (!plan->tuned_scale) {
+            const double keep = plan->class_scale[c];
+            double bsc = keep;
+            for (double sc : kTuneScales) {
+                if (sc == keep) continue;
+                plan->class_scale[c] = sc;
+                double ms = 0.0;
+                st = measure(&ms);
+                if (st != AIDW_OK) break;
+                if (ms < best) {
+                    best = ms;
+                    bsc = sc;
+                }
             }
+            plan->class_scale[c] = bsc;
+        }
+        const int keep_t = plan->class_threads[c];
+        int bth = keep_t;
+        for (int th : kTuneThreads) {
+            if (th == keep_t || st != AIDW_OK) continue;
+            plan->class_threads[c] = th;
+            double ms = 0.0;
+            st = measure(&ms);
             if (st != AIDW_OK) break;
             if (ms < best) {
                 best = ms;
-                best_scale = plan->cell_scale;
-                best_threads = th;
+                bth = th;
             }
         }
-        if (st != AIDW_OK) break;
+        plan->class_threads[c] = bth;
     }
     cudaEventDestroy(a);
     cudaEventDestroy(b);
-    plan->cell_scale = st == AIDW_OK ? best_scale : old_scale;
-    plan->knn_threads = st == AIDW_OK ? best_threads : old_threads;
+    if (st != AIDW_OK) {
+        for (int c = 0; c < kClasses; ++c) {
+            plan->class_scale[c] = old_scale[c];
+            plan->class_threads[c] = old_threads[c];
+        }
+    } else {
+        plan->tuned = 1;
+        cache_store(plan, best);
+    }
     layout_cells(plan);
     if (plan->exec) {
         cudaGraphExecDestroy(plan->exec);
@@ -655,18 +850,43 @@ aidw_status aidw_batch_plan_tune(aidw_batch_plan *plan, const aidw_job *jobs,
     return st;
 }
 
+// The class holding most queries (what aidw_batch_plan_get reports).
+static int main_class(const aidw_batch_plan *plan)
+{
+    int best = 0;
+    for (int c = 1; c < kClasses; ++c)
+        if (plan->kclass_q[c] > plan->kclass_q[best]) best = c;
+    return best;
+}
+
 aidw_status aidw_batch_plan_get(const aidw_batch_plan *plan, double *cell_scale,
                                 int *knn_threads, int64_t *total_pairs, int64_t *pool_bytes)
 {
     if (!plan) return AIDW_ERR_INVALID_ARG;
-    if (cell_scale) *cell_scale = plan->cell_scale;
-    if (knn_threads) *knn_threads = plan->knn_threads;
+    const int c = main_class(plan);
+    if (cell_scale) *cell_scale = plan->class_scale[c];
+    if (knn_threads) *knn_threads = plan->class_threads[c];
     if (total_pairs) {
         long long t = 0;
         for (int j = 0; j < plan->n_jobs; ++j) t += plan->n[j] * plan->m[j];
         *total_pairs = t;
     }
     if (pool_bytes) *pool_bytes = (int64_t)plan->pool_bytes;
+    return AIDW_OK;
+}
+
+aidw_status aidw_batch_plan_get_classes(const aidw_batch_plan *plan, int *kmax,
+                                        double *cell_scale, int *knn_threads, int64_t *queries,
+                                        int *source)
+{
+    if (!plan) return AIDW_ERR_INVALID_ARG;
+    for (int c = 0; c < kClasses; ++c) {
+        if (kmax) kmax[c] = kClassKmax[c];
+        if (cell_scale) cell_scale[c] = plan->class_scale[c];
+        if (knn_threads) knn_threads[c] = plan->class_threads[c];
+        if (queries) queries[c] = plan->kclass_q[c];
+    }
+    if (source) *source = plan->tuned;
     return AIDW_OK;
 }
 

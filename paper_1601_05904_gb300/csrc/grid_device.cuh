@@ -27,6 +27,9 @@ __device__ __forceinline__ float dec_float(int e)
     return __int_as_float(e >= 0 ? e : (e ^ 0x7FFFFFFF));
 }
 
+__device__ __forceinline__ void grid_dims(GridDev *g, double cell_scale, double area_param,
+                                          long long cap);
+
 __device__ __forceinline__ void grid_init(GridDev *g, long long n)
 {
     g->enc_min_x = 0x7FFFFFFF;
@@ -89,6 +92,102 @@ __device__ __forceinline__ void bbox_block(const float *__restrict__ x, const fl
         atomicMin(&g->enc_min_y, enc_float(mny));
         atomicMax(&g->enc_max_y, enc_float(mxy));
         if (sbad) atomicOr(&g->status, kStatusNonfiniteData);
+    }
+}
+
+// ---- bounding box and dimensions in one launch --------------------------------
+// Each block reduces its points to (min x, max x, min y, max y, non-finite
+// flag) and stores them in part[5 * block]; the last block to finish (an
+// atomic ticket, which it resets for the next launch) reduces the blocks'
+// records, writes the whole grid record (status included, so the record
+// needs no initialisation) and computes the dimensions.
+__device__ __forceinline__ void bbox_dims_block(const float *__restrict__ x,
+                                                const float *__restrict__ y,
+                                                const float *__restrict__ z, long long n,
+                                                float *__restrict__ part, int *ticket, GridDev *g,
+                                                double cell_scale, double area_param,
+                                                long long cap)
+{
+    float mnx = FLT_MAX, mny = FLT_MAX, mxx = -FLT_MAX, mxy = -FLT_MAX;
+    int bad = 0;
+    const long long stride = (long long)gridDim.x * blockDim.x;
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
+        const float xi = __ldg(x + i), yi = __ldg(y + i), zi = __ldg(z + i);
+        if (!isfinite(xi) || !isfinite(yi) || !isfinite(zi)) {
+            bad = 1;
+            continue;
+        }
+        mnx = fminf(mnx, xi);
+        mxx = fmaxf(mxx, xi);
+        mny = fminf(mny, yi);
+        mxy = fmaxf(mxy, yi);
+    }
+    __shared__ float s[5][kThreads / 32];
+    __shared__ bool last;
+    for (int round = 0; round < 2; ++round) {
+        for (int o = 16; o > 0; o >>= 1) {
+            mnx = fminf(mnx, __shfl_xor_sync(0xffffffffu, mnx, o));
+            mxx = fmaxf(mxx, __shfl_xor_sync(0xffffffffu, mxx, o));
+            mny = fminf(mny, __shfl_xor_sync(0xffffffffu, mny, o));
+            mxy = fmaxf(mxy, __shfl_xor_sync(0xffffffffu, mxy, o));
+        }
+        bad = __any_sync(0xffffffffu, bad);
+        const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+        if (l == 0) {
+            s[0][w] = mnx;
+            s[1][w] = mxx;
+            s[2][w] = mny;
+            s[3][w] = mxy;
+            s[4][w] = bad ? 1.0f : 0.0f;
+        }
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            for (int i = 1; i < kThreads / 32; ++i) {
+                mnx = fminf(mnx, s[0][i]);
+                mxx = fmaxf(mxx, s[1][i]);
+                mny = fminf(mny, s[2][i]);
+                mxy = fmaxf(mxy, s[3][i]);
+                bad |= s[4][i] != 0.0f;
+            }
+        }
+        if (round == 1) break;
+        if (threadIdx.x == 0) {
+            float *p = part + 5 * (long long)blockIdx.x;
+            p[0] = mnx;
+            p[1] = mxx;
+            p[2] = mny;
+            p[3] = mxy;
+            p[4] = bad ? 1.0f : 0.0f;
+            __threadfence();
+            last = atomicAdd(ticket, 1) == (int)gridDim.x - 1;
+        }
+        __syncthreads();
+        if (!last) return;
+        // the last block: every block's record is visible (each fenced
+        // before taking its ticket); reduce them with the same code
+        __threadfence();
+        mnx = mny = FLT_MAX;
+        mxx = mxy = -FLT_MAX;
+        bad = 0;
+        for (int b = threadIdx.x; b < (int)gridDim.x; b += blockDim.x) {
+            const float *p = part + 5 * (long long)b;
+            mnx = fminf(mnx, __ldcg(p + 0));
+            mxx = fmaxf(mxx, __ldcg(p + 1));
+            mny = fminf(mny, __ldcg(p + 2));
+            mxy = fmaxf(mxy, __ldcg(p + 3));
+            bad |= __ldcg(p + 4) != 0.0f;
+        }
+        __syncthreads();  // s[] is reused
+    }
+    if (threadIdx.x == 0) {
+        *ticket = 0;
+        g->enc_min_x = enc_float(mnx);
+        g->enc_max_x = enc_float(mxx);
+        g->enc_min_y = enc_float(mny);
+        g->enc_max_y = enc_float(mxy);
+        g->n_data = n;
+        g->status = bad ? kStatusNonfiniteData : 0;
+        grid_dims(g, cell_scale, area_param, cap);
     }
 }
 
@@ -281,6 +380,86 @@ __device__ __forceinline__ void scan_apply_chunk(int *__restrict__ a, long long 
         s += v[j];
     }
     int run = offset + block_exclusive_scan(s, tot);
+#pragma unroll
+    for (int j = 0; j < kScanItems; ++j) {
+        if (base + j < len) a[base + j] = run;
+        run += v[j];
+    }
+}
+
+// ---- single-pass exclusive scan (decoupled look-back) --------------------------
+// In-place exclusive scan of a[0, len) in chunks of kScanChunk, one chunk per
+// block, in one launch.  Blocks take their chunk from an atomic ticket, so
+// every chunk before a block's own belongs to a block that has already
+// started.  A block publishes its chunk sum (flag 1), looks back over the
+// preceding chunks' records (adding sums until it meets an inclusive
+// prefix, flag 2), publishes its own inclusive prefix and scans its chunk
+// from there.  Records are 64-bit (flag << 32 | value), written with release
+// and read with acquire semantics.  Waiting for a record that is not yet
+// published is bounded: after kLookbackTries reads the block sets
+// kStatusTimeout in *status and carries on (the result is then wrong and the
+// caller reports the error).  flags[] (one per chunk) and *ticket must be
+// zero before the launch; values are int32 (sums up to 2^31 - 1).
+constexpr int kLookbackTries = 1 << 22;
+
+__device__ __forceinline__ unsigned long long ld_acquire_u64(const unsigned long long *p)
+{
+    unsigned long long v;
+    asm volatile("ld.acquire.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
+    return v;
+}
+__device__ __forceinline__ void st_release_u64(unsigned long long *p, unsigned long long v)
+{
+    asm volatile("st.release.gpu.global.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
+}
+
+__device__ __forceinline__ void scan_lookback_block(int *__restrict__ a, long long len,
+                                                    unsigned long long *flags, int *ticket,
+                                                    int *status)
+{
+    __shared__ long long chunk_s;
+    __shared__ int prefix_s;
+    __shared__ int tot;
+    if (threadIdx.x == 0) chunk_s = atomicAdd(ticket, 1);
+    __syncthreads();
+    const long long chunk = chunk_s;
+    const long long base = chunk * kScanChunk + (long long)threadIdx.x * kScanItems;
+    int v[kScanItems];
+    int sum = 0;
+#pragma unroll
+    for (int j = 0; j < kScanItems; ++j) {
+        v[j] = (base + j < len) ? a[base + j] : 0;
+        sum += v[j];
+    }
+    const int ex = block_exclusive_scan(sum, tot);
+    if (threadIdx.x == 0) {
+        int prefix = 0;
+        if (chunk == 0) {
+            st_release_u64(flags, (2ull << 32) | (unsigned)tot);
+        } else {
+            st_release_u64(flags + chunk, (1ull << 32) | (unsigned)tot);
+            long long j = chunk - 1;
+            int tries = 0;
+            while (j >= 0) {
+                const unsigned long long r = ld_acquire_u64(flags + j);
+                const unsigned f = (unsigned)(r >> 32);
+                if (f == 0) {
+                    if (++tries > kLookbackTries) {
+                        atomicOr(status, kStatusTimeout);
+                        break;
+                    }
+                    continue;
+                }
+                prefix += (int)(unsigned)r;
+                if (f == 2) break;
+                --j;
+            }
+            st_release_u64(flags + chunk, (2ull << 32) | (unsigned)(prefix + tot));
+        }
+        prefix_s = prefix;
+    }
+    __syncthreads();
+    int run = prefix_s + ex;
 #pragma unroll
     for (int j = 0; j < kScanItems; ++j) {
         if (base + j < len) a[base + j] = run;

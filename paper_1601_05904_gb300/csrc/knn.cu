@@ -739,6 +739,8 @@ void launch_knn_k(const KnnJob &job0, const KnnJob *jobs, int n_jobs, long long 
         launch_knn<F64, 8>(job0, jobs, n_jobs, total_q, ap, threads, s);
     else if (kmax <= 16)
         launch_knn<F64, 16>(job0, jobs, n_jobs, total_q, ap, threads, s);
+    else if (kmax <= 24)
+        launch_knn<F64, 24>(job0, jobs, n_jobs, total_q, ap, threads, s);
     else
         launch_knn<F64, 32>(job0, jobs, n_jobs, total_q, ap, threads, s);
 }
@@ -761,19 +763,11 @@ __global__ void __launch_bounds__(gridk::kThreads)
     gridk::key_one_xy(i, x, y, g, count, key, rank);
 }
 
-__global__ void __launch_bounds__(gridk::kThreads) k_qscan_reduce(const int *a, long long len,
-                                                                   int *bsum)
+__global__ void __launch_bounds__(gridk::kThreads) k_qscan(int *a, long long len,
+                                                           unsigned long long *flags,
+                                                           int *ticket, GridDev *g)
 {
-    gridk::scan_reduce_chunk(a, len, blockIdx.x, bsum + blockIdx.x);
-}
-__global__ void __launch_bounds__(gridk::kThreads) k_qscan_sums(int *bsum, int nb)
-{
-    gridk::scan_sums(bsum, nb);
-}
-__global__ void __launch_bounds__(gridk::kThreads) k_qscan_apply(int *a, long long len,
-                                                                  const int *bsum)
-{
-    gridk::scan_apply_chunk(a, len, blockIdx.x, bsum[blockIdx.x]);
+    gridk::scan_lookback_block(a, len, flags, ticket, &g->status);
 }
 __global__ void __launch_bounds__(gridk::kThreads)
     k_qscatter(long long nq, const int *__restrict__ start, const int *__restrict__ key,
@@ -802,28 +796,28 @@ aidw_status query_order(const aidw_grid *g, const float *qx, const float *qy, lo
     using namespace gridk;
     const long long len = g->cap_cells + 1;
     const long long nb = (len + kScanChunk - 1) / kScanChunk;
-    int *count = nullptr, *key = nullptr, *rank = nullptr, *bsum = nullptr;
+    const long long n_ints = grid_cell_start_ints(g->cap_cells);  // counts, scan records, tickets
+    const long long rec_off = (len + 1) / 2 * 2;
+    int *count = nullptr, *key = nullptr, *rank = nullptr;
     *order = nullptr;
-    cudaError_t e = lib_alloc((void **)&count, sizeof(int) * len, s);
+    cudaError_t e = lib_alloc((void **)&count, sizeof(int) * n_ints, s);
     if (e == cudaSuccess) e = lib_alloc((void **)&key, sizeof(int) * nq, s);
     if (e == cudaSuccess) e = lib_alloc((void **)&rank, sizeof(int) * nq, s);
-    if (e == cudaSuccess) e = lib_alloc((void **)&bsum, sizeof(int) * nb, s);
     if (e == cudaSuccess) e = lib_alloc((void **)order, sizeof(int) * nq, s);
     if (e == cudaSuccess) {
         const unsigned qb = (unsigned)((nq + kThreads - 1) / kThreads);
-        cudaMemsetAsync(count, 0, sizeof(int) * len, s);
+        unsigned long long *flags = reinterpret_cast<unsigned long long *>(count + rec_off);
+        int *ticket = count + rec_off + 2 * nb;
+        cudaMemsetAsync(count, 0, sizeof(int) * n_ints, s);
         k_qkeys<<<qb, kThreads, 0, s>>>(qx, qy, nq, g->dev, count, key, rank);
-        k_qscan_reduce<<<(unsigned)nb, kThreads, 0, s>>>(count, len, bsum);
-        k_qscan_sums<<<1, kThreads, 0, s>>>(bsum, (int)nb);
-        k_qscan_apply<<<(unsigned)nb, kThreads, 0, s>>>(count, len, bsum);
+        k_qscan<<<(unsigned)nb, kThreads, 0, s>>>(count, len, flags, ticket, g->dev);
         k_qscatter<<<qb, kThreads, 0, s>>>(nq, count, key, rank, *order);
-        *launches += 5;
+        *launches += 3;
         e = cudaGetLastError();
     }
     lib_free(count, s);
     lib_free(key, s);
     lib_free(rank, s);
-    lib_free(bsum, s);
     if (e != cudaSuccess) {
         lib_free(*order, s);
         *order = nullptr;

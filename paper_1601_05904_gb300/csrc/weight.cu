@@ -107,6 +107,8 @@ struct SKArgs {
     long long G;        // CTAs
     long long total_q;  // queries of all jobs
     int *status;
+    int *fail;          // this launch's failure flag: zeroed before the launch, set by a
+                        // CTA whose wait expired; the finalize then writes NaN
     int wait_tries;     // bound of every mbarrier wait (tries; hook launches only)
     long long skip_unit;  // test hook: the data tile of this unit is never
                           // copied, so its wait expires (-1: none)
@@ -155,35 +157,6 @@ __device__ __forceinline__ int aos_count(long long n_pad, long long d)
     return (int)min((long long)kDTile, n_pad - d * kDTile);
 }
 
-// After an expired wait the partial sums of the query tiles this CTA had not
-// finished (the current one and the later ones of its share) are unknown, so
-// its slots for them are set to NaN: the finalize step then returns NaN for
-// exactly the queries whose sum is incomplete, instead of adding whatever an
-// earlier launch left in those slots.  Called by every thread of the CTA.
-__device__ __forceinline__ void nan_part(float4 &p)
-{
-    const float nan = __int_as_float(0x7fc00000);
-    p = make_float4(nan, nan, nan, nan);
-}
-__device__ __forceinline__ void nan_part(double2 &p)
-{
-    const double nan = __longlong_as_double(0x7ff8000000000000LL);
-    p = make_double2(nan, nan);
-}
-template <typename Part, int QTILE, int NT>
-__device__ void poison_rest(const SKArgs &a, Part *part, long long cta, long long u, long long u1)
-{
-    Part bad;
-    nan_part(bad);
-    while (u < u1) {
-        const WJob J = job_of_unit(a, u);
-        const long long t = (u - J.unit_base) / J.D;
-        const long long slot = J.tile_base + t + cta;
-        for (int i = threadIdx.x; i < QTILE; i += NT) part[slot * QTILE + i] = bad;
-        u = J.unit_base + (t + 1) * J.D;  // first unit of the next query tile
-    }
-}
-
 template <bool HOOK>
 __device__ __forceinline__ void issue_tile_soa(const SKArgs &a, float *buf, uint64_t *bar,
                                                long long u)
@@ -224,7 +197,7 @@ __device__ __forceinline__ void issue_tile_aos(const SKArgs &a, Point *buf, uint
 // is the bound; moving part of the work to the FMA pipe balances the two.
 // HOOK: the instantiation launched only while the timeout test hook is armed
 // (aidw_test_expire_next_wait); the normal kernel has no trace of it.
-template <int PE, int PL, bool HOOK = false, int THREADS = WCfg<false>::kThreads,
+template <int PE, int PL, bool HOOK = false, int PE2 = PE, int THREADS = WCfg<false>::kThreads,
           int Q = WCfg<false>::kQPT, int MINB = WCfg<false>::kMinBlocks>
 __global__ void __launch_bounds__(THREADS, MINB)
     k_weight_f32(SKArgs a, float4 *__restrict__ part)
@@ -292,7 +265,11 @@ __global__ void __launch_bounds__(THREADS, MINB)
 #pragma unroll
                     for (int i = 0; i < Q; ++i) ps[i] = pz[i] = zero2;
 #pragma unroll 16
-                    for (int jj = c0; jj < c0 + kChunk2; jj += 4) {
+                    for (int st = 0; st < kChunk2 / 4; ++st) {
+                        // steps alternate between PE and PE2 exp2 products on the
+                        // FMA pipe (the parity is a constant in each unrolled copy)
+                        const int pe = (st & 1) ? PE2 : PE;
+                        const int jj = c0 + 4 * st;
                         const float4 xv = *reinterpret_cast<const float4 *>(X + jj);
                         const float4 yv = *reinterpret_cast<const float4 *>(Y + jj);
                         const float4 zv = *reinterpret_cast<const float4 *>(Z + jj);
@@ -316,7 +293,7 @@ __global__ void __launch_bounds__(THREADS, MINB)
                                 }
                                 const F2 tt = f2_fma(lg, c2[i], b2[i]);
                                 F2 w;
-                                if (h * Q + i < PE) {
+                                if (h * Q + i < pe) {
                                     w = f2_exp2_poly(tt);
                                 } else {
                                     float t0, t1;
@@ -337,14 +314,16 @@ __global__ void __launch_bounds__(THREADS, MINB)
             }
             // every thread is done with stage s before it is refilled
             if (__syncthreads_or(!ok)) {
-                if (threadIdx.x == 0) atomicOr(a.status, kStatusTimeout);
+                if (threadIdx.x == 0) {
+                    atomicOr(a.status, kStatusTimeout);
+                    atomicOr(a.fail, 1);
+                }
                 // drain the copies this CTA still has in flight, then leave
                 if (threadIdx.x == 0)
                     for (long long v = u; v < min(u1, u + kStages); ++v)
                         mbar_wait_bounded(&full[(v - u0) % kStages],
                                           (uint32_t)(((v - u0) / kStages) & 1), wait_tries);
                 __syncthreads();
-                poison_rest<float4, C::kQTile, THREADS>(a, part, cta, u, u1);
                 return;
             }
             if (threadIdx.x == 0 && u + kStages < u1)
@@ -377,7 +356,7 @@ __global__ void k_finalize_f32(SKArgs a, const float4 *__restrict__ part)
     const long long q = gq - J.q_base;
     float *out_z = static_cast<float *>(J.out_z);
     const QRec r = J.recs[q];
-    if (!(r.alpha == r.alpha)) {
+    if (!(r.alpha == r.alpha) || *a.fail) {  // non-finite query, or a sum cut short
         out_z[q] = __int_as_float(0x7fc00000);
         return;
     }
@@ -463,13 +442,15 @@ __global__ void __launch_bounds__(WCfg<true>::kThreads, WCfg<true>::kMinBlocks)
                 }
             }
             if (__syncthreads_or(!ok)) {
-                if (threadIdx.x == 0) atomicOr(a.status, kStatusTimeout);
+                if (threadIdx.x == 0) {
+                    atomicOr(a.status, kStatusTimeout);
+                    atomicOr(a.fail, 1);
+                }
                 if (threadIdx.x == 0)
                     for (long long v = u; v < min(u1, u + kStages); ++v)
                         mbar_wait_bounded(&full[(v - u0) % kStages],
                                           (uint32_t)(((v - u0) / kStages) & 1), wait_tries);
                 __syncthreads();
-                poison_rest<double2, C::kQTile, C::kThreads>(a, part, cta, u, u1);
                 return;
             }
             if (threadIdx.x == 0 && u + kStages < u1)
@@ -492,8 +473,8 @@ __global__ void k_finalize_f64(SKArgs a, const double2 *__restrict__ part)
     const long long q = gq - J.q_base;
     double *out_z = static_cast<double *>(J.out_z);
     const QRec r = J.recs[q];
-    if (!(r.alpha == r.alpha)) {
-        out_z[q] = r.alpha;
+    if (!(r.alpha == r.alpha) || *a.fail) {  // non-finite query, or a sum cut short
+        out_z[q] = __longlong_as_double(0x7ff8000000000000LL);
         return;
     }
     if (r.n_hit > 0) {
@@ -513,29 +494,35 @@ __global__ void k_finalize_f64(SKArgs a, const double2 *__restrict__ part)
 }
 
 // Polynomial split of the float32 kernel: products per inner step whose exp2
-// (first number) and lg2 (second) run on the FMA pipe.  Measured on GB300 at
+// (first number) and lg2 (second) run on the FMA pipe, and (third) the exp2
+// products of every second step where steps alternate.  Measured on GB300 at
 // n = m = 1M (weighting ms, 64-point chunks, point loop unrolled 16x):
 // {2,0} 334.8, {0,0} 352.4, {3,0} 354.8, {4,0} 382.1, {0,1} 345.3,
-// {1,1} 348.3, {0,2} 369.2, so {2,0} is the default.  AIDW_WEIGHT_POLY ("E,L") selects another entry of the table,
-// for measuring the balance on a given GPU.
+// {1,1} 348.3, {0,2} 369.2, so {2,0} is the default.  AIDW_WEIGHT_POLY
+// ("E,L" or "E,L,E2") selects another entry of the table, for measuring the
+// balance on a given GPU.
 using F32Kernel = void (*)(SKArgs, float4 *);
 struct PolySplit {
-    int e, l;
+    int e, l, e2;
     F32Kernel kernel;
 };
 const PolySplit kPolySplits[] = {
-    {2, 0, k_weight_f32<2, 0>}, {0, 0, k_weight_f32<0, 0>}, {3, 0, k_weight_f32<3, 0>},
-    {4, 0, k_weight_f32<4, 0>}, {0, 1, k_weight_f32<0, 1>}, {1, 1, k_weight_f32<1, 1>},
-    {0, 2, k_weight_f32<0, 2>}};
+    {2, 0, 2, k_weight_f32<2, 0>}, {0, 0, 0, k_weight_f32<0, 0>}, {3, 0, 3, k_weight_f32<3, 0>},
+    {4, 0, 4, k_weight_f32<4, 0>}, {0, 1, 0, k_weight_f32<0, 1>}, {1, 1, 1, k_weight_f32<1, 1>},
+    {0, 2, 0, k_weight_f32<0, 2>}, {2, 0, 3, k_weight_f32<2, 0, false, 3>},
+    {1, 0, 2, k_weight_f32<1, 0, false, 2>}};
 constexpr int kNumPolySplits = (int)(sizeof(kPolySplits) / sizeof(kPolySplits[0]));
 const PolySplit &f32_split()
 {
     static const int idx = [] {
         const char *e = getenv("AIDW_WEIGHT_POLY");
-        int pe = -1, pl = -1;
-        if (e && sscanf(e, "%d,%d", &pe, &pl) == 2)
+        int pe = -1, pl = -1, pe2 = -1;
+        const int got = e ? sscanf(e, "%d,%d,%d", &pe, &pl, &pe2) : 0;
+        if (got == 2) pe2 = pe;
+        if (got >= 2)
             for (int i = 0; i < kNumPolySplits; ++i)
-                if (kPolySplits[i].e == pe && kPolySplits[i].l == pl) return i;
+                if (kPolySplits[i].e == pe && kPolySplits[i].l == pl && kPolySplits[i].e2 == pe2)
+                    return i;
         return 0;
     }();
     return kPolySplits[idx];
@@ -622,6 +609,7 @@ aidw_status launch(SKArgs a, void *part, cudaStream_t s)
     using Part = typename C::Part;
     const size_t smem = stage_smem<F64>();
     int prof = profile_begin(s);
+    cudaMemsetAsync(a.fail, 0, sizeof(int), s);
     if (F64) {
         if (a.skip_unit >= 0)
             k_weight_f64<true><<<(unsigned)a.G, C::kThreads, smem, s>>>(a, static_cast<double2 *>(part));
@@ -682,7 +670,8 @@ aidw_status run(const aidw_grid *g, const float *qx, const float *qy, long long 
     a.G = std::min<long long>(resident_ctas<F64>(g->device), a.U);
     void *part = nullptr;
     const size_t part_bytes = sizeof(typename C::Part) * (size_t)C::kQTile * (size_t)(a.job0.T + a.G);
-    if (lib_alloc(&part, part_bytes, s) != cudaSuccess) return AIDW_ERR_OOM;
+    if (lib_alloc(&part, part_bytes + 256, s) != cudaSuccess) return AIDW_ERR_OOM;
+    a.fail = reinterpret_cast<int *>(static_cast<unsigned char *>(part) + part_bytes);
     const aidw_status st = launch<F64>(a, part, s);
     lib_free(part, s);
     return st;
@@ -696,9 +685,12 @@ aidw_status run_scratch(const aidw_grid *g, const float *qx, const float *qy, lo
     using C = WCfg<F64>;
     SKArgs a = single_job<F64>(g, qx, qy, nq, recs, out_z);
     const long long slot_bytes = (long long)sizeof(typename C::Part) * C::kQTile;
-    const long long g_fit = (long long)(scratch_bytes / (size_t)slot_bytes) - a.job0.T;
+    if (scratch_bytes < 512) return AIDW_ERR_INVALID_ARG;
+    const size_t part_room = scratch_bytes - 256;  // the last 256 bytes hold the flag
+    const long long g_fit = (long long)(part_room / (size_t)slot_bytes) - a.job0.T;
     if (g_fit < 1) return AIDW_ERR_INVALID_ARG;
     a.G = std::min<long long>(std::min<long long>(resident_ctas<F64>(g->device), a.U), g_fit);
+    a.fail = reinterpret_cast<int *>(static_cast<unsigned char *>(scratch) + part_room);
     return launch<F64>(a, scratch, s);
 }
 
@@ -706,10 +698,11 @@ aidw_status run_scratch(const aidw_grid *g, const float *qx, const float *qy, lo
 
 void weight_mix(int *products, int *poly_exp2, int *poly_lg2, double *fma_lanes, double *instr)
 {
+    // counted over two inner steps (the period of an alternating split)
     const PolySplit &sp = f32_split();
-    if (products) *products = 2 * WCfg<false>::kQPT;
-    if (poly_exp2) *poly_exp2 = sp.e;
-    if (poly_lg2) *poly_lg2 = sp.l;
+    if (products) *products = 2 * 2 * WCfg<false>::kQPT;
+    if (poly_exp2) *poly_exp2 = sp.e + sp.e2;
+    if (poly_lg2) *poly_lg2 = 2 * sp.l;
     for (int i = 0; i < 3; ++i) {
         if (fma_lanes) fma_lanes[i] = kFmaLanes[i];
         if (instr) instr[i] = kInstr[i];
@@ -763,7 +756,7 @@ aidw_status weight_launch(const aidw_grid *g, const float *qx, const float *qy,
 
 aidw_status weight_launch_batch(const WJob *jobs, int n_jobs, long long total_u,
                                 long long total_q, bool fp64, void *part, long long G,
-                                int *status, int device, cudaStream_t s)
+                                int *status, int *fail, int device, cudaStream_t s)
 {
     if (total_u <= 0 || total_q <= 0) return AIDW_OK;
     SKArgs a;
@@ -774,6 +767,7 @@ aidw_status weight_launch_batch(const WJob *jobs, int n_jobs, long long total_u,
     a.G = std::max<long long>(1, std::min<long long>(G, total_u));
     a.total_q = total_q;
     a.status = status;
+    a.fail = fail;
     (void)device;
     return fp64 ? launch<true>(a, part, s) : launch<false>(a, part, s);
 }

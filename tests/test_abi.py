@@ -112,11 +112,12 @@ def test_binding_fails_loudly_without_library(tmp_path):
 
 def test_weight_mix_is_host_only(lib):
     """The weighting loop's instruction mix (roofline accounting) answers
-    without a GPU; the default split takes 2 of 8 exp2s from the FMA pipe."""
+    without a GPU; the default split takes 4 of 16 exp2s (over two inner
+    steps) from the FMA pipe."""
     from paper_1601_05904_gb300 import binding
     mix = binding.aidw_weight_mix()
-    assert mix["products"] == 8
-    assert (mix["poly_exp2"], mix["poly_lg2"]) == (2, 0)
+    assert mix["products"] == 16
+    assert (mix["poly_exp2"], mix["poly_lg2"]) == (4, 0)
     assert mix["fma_lanes"] == {"base": 7.0, "exp2_poly": 8.0, "lg2_poly": 10.0}
     assert mix["instr"]["base"] == 3.5
 

@@ -57,3 +57,30 @@ def test_uniform_data_rarely_falls_back():
     lo = x.min()
     cw = 2.0 * 1000.0 / (2.0 * np.sqrt(1 << 20))   # a typical cell width, 2 r_exp
     assert _check(x, lo, cw) < 2e-3
+
+
+
+def test_fma_pipe_polynomials_are_the_generators_fits():
+    """The exp2 / log2 polynomial coefficients in the kernel source are the
+    float32-rounded minimax fits that fit_poly.py computes, and meet their
+    stated error bounds (the generator, not the kernel, is under test: its
+    output is what the kernel must carry)."""
+    import os
+    import re
+
+    from paper_1601_05904_gb300 import fit_poly
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    src = open(os.path.join(root, "paper_1601_05904_gb300", "csrc", "aidw_device.cuh")).read()
+
+    def consts(fn):
+        body = src[src.index(f"__device__ __forceinline__ F2 {fn}("):]
+        body = body[: body.index("\n}\n")]
+        # coefficients are the scientific-notation literals packed into both lanes
+        return [float(np.float32(v)) for v in re.findall(r"f2_pack\(([-+0-9.]+e[-+0-9]+)f, \1f\)", body)]
+    e = consts("f2_exp2_poly")
+    lg = consts("f2_log2_poly")
+    assert len(e) == 6 and len(lg) == 8
+    assert e == [float(v) for v in fit_poly.exp2_coefficients().astype(np.float32)]
+    assert lg == [float(v) for v in fit_poly.log2_coefficients().astype(np.float32)]
+    assert fit_poly.exp2_error(np.array(e)) < 2e-7
+    assert fit_poly.log2_error(np.array(lg)) < 6e-8

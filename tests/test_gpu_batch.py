@@ -143,3 +143,87 @@ def test_batch_errors(aidw):
     x, y, z, qx, qy, k = raw[0]
     assert np.isfinite(host(outs[0])).all()
     plan.destroy()
+
+
+SPEC_CLASSES = [(6000, 2000, 8, 0.5), (6000, 2000, 12, 0.0), (4000, 2500, 20, 0.7),
+                (3000, 1000, 32, 0.2)] * 2
+
+
+def test_tuning_per_top_k_class_and_cache(aidw, oracle):
+    """Jobs fall into the top-k classes 8/16/24/32; the tuner chooses a cell
+    scale and kNN block size per class; a new plan for jobs of the same
+    shapes starts from the cached choice; results stay within tolerance."""
+    p = aidw.Params(k=10)
+    jobs, raw = _jobs(aidw, SPEC_CLASSES, seed=9)
+    plan = aidw.aidw_batch_plan_create(jobs, p)
+    info = aidw.aidw_batch_plan_get_classes(plan)
+    assert info["source"] == "defaults"
+    cls = info["classes"]
+    assert [c["kmax"] for c in cls] == [8, 16, 24, 32]
+    assert [c["queries"] for c in cls] == [4000, 4000, 5000, 2000]
+    assert [c["cell_scale"] for c in cls] == [2.0, 2.0, 3.0, 3.0]
+    aidw.aidw_batch_plan_tune(plan, jobs)
+    tuned = aidw.aidw_batch_plan_get_classes(plan)
+    assert tuned["source"] == "tuner"
+    for c in tuned["classes"]:
+        assert c["cell_scale"] in (1.0, 1.5, 2.0, 3.0, 4.0)
+        assert c["knn_threads"] in (0, 64, 128, 256)
+    outs = aidw.aidw_batch_run(plan, jobs)
+    assert aidw.aidw_batch_plan_status(plan) == 0
+    for (x, y, z, qx, qy, k), o in zip(raw, outs):
+        ref = oracle.aidw(x, y, z, qx, qy, k)
+        assert oracle.normalized_error(host(o), ref["z"], ref["scale"]).max() <= TOL_FP32
+    plan.destroy()
+    # same shapes, other data: the cached tuning applies at creation
+    jobs2, raw2 = _jobs(aidw, SPEC_CLASSES, seed=10)
+    plan2 = aidw.aidw_batch_plan_create(jobs2, p)
+    cached = aidw.aidw_batch_plan_get_classes(plan2)
+    assert cached["source"] == "cache"
+    assert cached["classes"] == tuned["classes"]
+    outs = aidw.aidw_batch_run(plan2, jobs2)
+    assert aidw.aidw_batch_plan_status(plan2) == 0
+    for (x, y, z, qx, qy, k), o in zip(raw2, outs):
+        ref = oracle.aidw(x, y, z, qx, qy, k)
+        assert oracle.normalized_error(host(o), ref["z"], ref["scale"]).max() <= TOL_FP32
+    plan2.destroy()
+
+
+_CACHE_SCRIPT = r"""
+import json, sys
+sys.path.insert(0, {root!r})
+sys.path.insert(0, {tests!r})
+import paper_1601_05904_gb300 as aidw
+from test_gpu_batch import SPEC_CLASSES, _jobs
+aidw.load()
+jobs, _ = _jobs(aidw, SPEC_CLASSES, seed=11)
+plan = aidw.aidw_batch_plan_create(jobs, aidw.Params(k=10))
+if sys.argv[1] == "tune":
+    aidw.aidw_batch_plan_tune(plan, jobs)
+print(json.dumps(aidw.aidw_batch_plan_get_classes(plan)))
+plan.destroy()
+"""
+
+
+def test_tuning_cache_file_reaches_a_new_process(tmp_path):
+    """With AIDW_TUNE_CACHE=<file>, a tuning measured in one process is the
+    starting choice of a plan for the same shapes in the next process."""
+    import json
+    import os
+    import subprocess
+    import sys
+    tests = os.path.dirname(os.path.abspath(__file__))
+    script = tmp_path / "cache_probe.py"
+    script.write_text(_CACHE_SCRIPT.format(root=os.path.dirname(tests), tests=tests))
+    env = dict(os.environ, AIDW_TUNE_CACHE=str(tmp_path / "tune.txt"))
+
+    def run(mode):
+        r = subprocess.run([sys.executable, str(script), mode], capture_output=True, text=True,
+                           env=env, timeout=600)
+        assert r.returncode == 0, r.stderr[-2000:]
+        return json.loads(r.stdout.strip().splitlines()[-1])
+    first = run("tune")
+    assert first["source"] == "tuner"
+    assert (tmp_path / "tune.txt").read_text().count("\n") == 1
+    second = run("create")
+    assert second["source"] == "cache"
+    assert second["classes"] == first["classes"]

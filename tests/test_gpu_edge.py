@@ -222,9 +222,9 @@ def test_interpolate_replays_in_a_cuda_graph(aidw, oracle):
 def test_expired_wait_reports_timeout_and_gpu_stays_usable(aidw, oracle):
     """The weighting kernel's bounded data-tile wait: a copy that is never
     issued makes the wait expire (50 tries); the kernel latches the timeout,
-    drains its own copies, marks its unfinished sums NaN and returns: the
-    queries it cut short are NaN, the others correct; the next call is
-    correct."""
+    sets the launch's failure flag, drains its own copies and returns; that
+    call's predictions are all NaN (no partial sum cut short reaches the
+    output); the next call is correct."""
     w = inputs.uniform_kilo(n=20000, m=3000, seed=64)
     ref = oracle.aidw(w.x, w.y, w.z, w.qx, w.qy, 10)
     for fp64 in (False, True):
@@ -235,11 +235,7 @@ def test_expired_wait_reports_timeout_and_gpu_stays_usable(aidw, oracle):
         z0, _ = aidw.aidw_interpolate(g, dev(w.qx), dev(w.qy), pp)
         assert aidw.aidw_grid_status(g) == 6          # AIDW_ERR_TIMEOUT
         assert aidw.aidw_grid_status(g) == 0          # cleared
-        z0 = host(z0)
-        bad = np.isnan(z0)
-        assert 0 < bad.sum() < w.m
-        err = oracle.normalized_error(z0[~bad], ref["z"][~bad], ref["scale"][~bad])
-        assert err.max() <= tol
+        assert np.isnan(host(z0)).all()
         z, _ = aidw.aidw_interpolate(g, dev(w.qx), dev(w.qy), pp)
         assert aidw.aidw_grid_status(g) == 0
         assert oracle.normalized_error(host(z), ref["z"], ref["scale"]).max() <= tol
