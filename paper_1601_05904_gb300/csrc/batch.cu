@@ -270,6 +270,18 @@ struct aidw_batch_plan {
 
 namespace {
 
+// Whether the per-class kNN launches run as parallel branches (default) or
+// one after another on the launching stream (AIDW_BATCH_BRANCHES=0), for
+// measuring the two forms.
+bool batch_knn_branches()
+{
+    static const bool on = [] {
+        const char *e = getenv("AIDW_BATCH_BRANCHES");
+        return !(e && atoi(e) == 0);
+    }();
+    return on;
+}
+
 // Recomputes the cell-width dependent part of the layout (caps, chunks).
 void layout_cells(aidw_batch_plan *P)
 {
@@ -358,7 +370,7 @@ aidw_status enqueue(aidw_batch_plan *P, cudaStream_t s, bool knn_only)
         const int b = P->kclass_begin[c], e = P->kclass_begin[c + 1];
         if (e == b) continue;
         cudaStream_t cs = s;
-        if (first < 0) {
+        if (first < 0 || !batch_knn_branches()) {
             first = c;
         } else {
             if (!forked) {
