@@ -234,7 +234,8 @@ aidw_status aidw_batch_run(aidw_batch_plan *plan, const aidw_job *jobs, aidw_str
  * launch of the smallest class whose register slots (8, 16, 24, 32) hold
  * its k.  Each class has its own cell-width scale (of its jobs' grids) and
  * kNN block size; the defaults are the single-grid choices (scale 2 up to
- * k = 16, 3 above; 128-thread blocks). */
+ * k = 16, 3 above; 128-thread blocks).  The classes' kNN launches run one
+ * after another (AIDW_BATCH_BRANCHES=1 runs them as parallel branches). */
 #define AIDW_BATCH_CLASSES 4
 
 /* Autotuner: times the grid build + kNN of all jobs (two runs per candidate,

@@ -391,12 +391,13 @@ __device__ __forceinline__ void scan_apply_chunk(int *__restrict__ a, long long 
 // In-place exclusive scan of a[0, len) in chunks of kScanChunk, one chunk per
 // block, in one launch.  Blocks take their chunk from an atomic ticket, so
 // every chunk before a block's own belongs to a block that has already
-// started.  A block publishes its chunk sum (flag 1), looks back over the
-// preceding chunks' records (adding sums until it meets an inclusive
-// prefix, flag 2), publishes its own inclusive prefix and scans its chunk
-// from there.  Records are 64-bit (flag << 32 | value), written with release
-// and read with acquire semantics.  Waiting for a record that is not yet
-// published is bounded: after kLookbackTries reads the block sets
+// started.  A block publishes its chunk sum (flag 1), then its first warp
+// looks back over the preceding chunks' records 32 at a time (lane i reads
+// the i-th nearest), adding sums up to the nearest inclusive prefix (flag
+// 2); the block publishes its own inclusive prefix and scans its chunk from
+// there.  Records are 64-bit (flag << 32 | value), written with release and
+// read with acquire semantics.  Waiting for a record that is not yet
+// published is bounded: after kLookbackTries rounds the block sets
 // kStatusTimeout in *status and carries on (the result is then wrong and the
 // caller reports the error).  flags[] (one per chunk) and *ticket must be
 // zero before the launch; values are int32 (sums up to 2^31 - 1).
@@ -432,31 +433,41 @@ __device__ __forceinline__ void scan_lookback_block(int *__restrict__ a, long lo
         sum += v[j];
     }
     const int ex = block_exclusive_scan(sum, tot);
-    if (threadIdx.x == 0) {
+    if (threadIdx.x < 32) {
+        const int lane = threadIdx.x;
         int prefix = 0;
         if (chunk == 0) {
-            st_release_u64(flags, (2ull << 32) | (unsigned)tot);
+            if (lane == 0) st_release_u64(flags, (2ull << 32) | (unsigned)tot);
         } else {
-            st_release_u64(flags + chunk, (1ull << 32) | (unsigned)tot);
-            long long j = chunk - 1;
+            if (lane == 0) st_release_u64(flags + chunk, (1ull << 32) | (unsigned)tot);
+            long long j = chunk - 1;  // nearest predecessor not yet added
             int tries = 0;
-            while (j >= 0) {
-                const unsigned long long r = ld_acquire_u64(flags + j);
+            for (;;) {
+                const long long at = j - lane;
+                // chunk 0 always publishes an inclusive prefix, so a window
+                // reaching below it never needs those lanes
+                const unsigned long long r = at >= 0 ? ld_acquire_u64(flags + at) : (2ull << 32);
                 const unsigned f = (unsigned)(r >> 32);
-                if (f == 0) {
+                const unsigned inc = __ballot_sync(0xffffffffu, f == 2);
+                const unsigned pending = __ballot_sync(0xffffffffu, f == 0);
+                const int first = inc ? __ffs(inc) - 1 : 31;           // lanes 0..first are needed
+                const unsigned need = first == 31 ? 0xffffffffu : ((2u << first) - 1u);
+                if (pending & need) {
                     if (++tries > kLookbackTries) {
-                        atomicOr(status, kStatusTimeout);
+                        if (lane == 0) atomicOr(status, kStatusTimeout);
                         break;
                     }
                     continue;
                 }
-                prefix += (int)(unsigned)r;
-                if (f == 2) break;
-                --j;
+                int add = lane <= first ? (int)(unsigned)r : 0;
+                for (int o = 16; o > 0; o >>= 1) add += __shfl_xor_sync(0xffffffffu, add, o);
+                prefix += add;
+                if (inc) break;
+                j -= 32;
             }
-            st_release_u64(flags + chunk, (2ull << 32) | (unsigned)(prefix + tot));
+            if (lane == 0) st_release_u64(flags + chunk, (2ull << 32) | (unsigned)(prefix + tot));
         }
-        prefix_s = prefix;
+        if (lane == 0) prefix_s = prefix;
     }
     __syncthreads();
     int run = prefix_s + ex;
