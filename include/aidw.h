@@ -160,6 +160,21 @@ aidw_status aidw_interpolate(const aidw_grid *g, const float *qx, const float *q
                              int64_t n_query, const aidw_params *p, void *out_z,
                              void *out_alpha, aidw_stream_t stream);
 
+/* End to end from HOST memory: the path of aidw_grid_build + aidw_interpolate
+ * for a caller whose arrays live on the host.  x, y, z [n_data] and qx, qy
+ * [n_query] are host float32 arrays (pageable or pinned; pinned ones copy
+ * asynchronously at full link speed); out_z (and out_alpha, if not NULL)
+ * [n_query] are host arrays of float32 (AIDW_FP32_COMP) or float64
+ * (AIDW_FP64_PLAIN).  The call copies the inputs to the current device,
+ * builds the grid, interpolates, copies the results back and waits for
+ * `stream`; device memory comes from the library's pool and is returned
+ * before the call ends.  Returns the first error, including a device error
+ * latched during the call (as aidw_grid_status). */
+aidw_status aidw_interpolate_host(const float *x, const float *y, const float *z, int64_t n_data,
+                                  const float *qx, const float *qy, int64_t n_query,
+                                  const aidw_params *p, void *out_z, void *out_alpha,
+                                  aidw_stream_t stream);
+
 /* ---- query sharding over several GPUs --------------------------------------
  * Every query is computed independently given all data points (the
  * one-thread-per-query decomposition of Sec. 4.2), so one query set splits
@@ -249,7 +264,8 @@ aidw_status aidw_batch_run(aidw_batch_plan *plan, const aidw_job *jobs, aidw_str
  * buckets of n_data and n_query, and k); aidw_batch_plan_create applies a
  * cached tuning to a plan with the same key.  With the environment variable
  * AIDW_TUNE_CACHE=<file> entries are also loaded from and appended to that
- * file. */
+ * file, one JSON object per line ({"key", "cell_scale": [4],
+ * "knn_threads": [4], "build_knn_ms"}). */
 aidw_status aidw_batch_plan_tune(aidw_batch_plan *plan, const aidw_job *jobs,
                                  aidw_stream_t stream, double *best_ms);
 

@@ -134,6 +134,8 @@ def load(path: str | None = None):
         lib.aidw_profile_read.argtypes = [P(ctypes.c_double), P(ctypes.c_int64)]
         lib.aidw_probe_pipe_rates.restype = c_int
         lib.aidw_probe_pipe_rates.argtypes = [P(ctypes.c_double)] * 3
+        lib.aidw_interpolate_host.restype = c_int
+        lib.aidw_interpolate_host.argtypes = [vp, vp, vp, i64, vp, vp, i64, P(CParams), vp, vp, vp]
         lib.aidw_shard_range.restype = c_int
         lib.aidw_shard_range.argtypes = [i64, c_int, c_int, P(i64), P(i64)]
         lib.aidw_interpolate_shard.restype = c_int
@@ -548,24 +550,34 @@ def aidw_batch(jobs, params: Params | None = None, stream=None):
     return [j.out_z for j in jobs]
 
 
-def interpolate_host(x, y, z, qx, qy, params: Params | None = None, stream=None):
-    """End-to-end call from host arrays: copies the inputs to the device,
-    builds the grid, interpolates and copies the predictions back.
+def interpolate_host(x, y, z, qx, qy, params: Params | None = None, stream=None,
+                     want_alpha: bool = False):
+    """End-to-end call from host arrays (aidw_interpolate_host): the library
+    copies the inputs to the current device, builds the grid, interpolates
+    and copies the predictions back.
 
-    Inputs may be numpy arrays or CPU tensors (pinned tensors copy
-    asynchronously).  Returns a CPU tensor of predictions."""
+    Inputs are numpy arrays or CPU tensors of float32 (pinned tensors copy
+    asynchronously).  Returns a CPU tensor of predictions (float32, or
+    float64 for AIDW_FP64_PLAIN), pinned, or (z, alpha) with want_alpha."""
+    import numpy as np
     import torch
-    dev = torch.device("cuda", torch.cuda.current_device())
+    p = params or Params()
 
-    def to_dev(a):
-        t = a if isinstance(a, torch.Tensor) else torch.from_numpy(a)
-        return t.to(dev, dtype=torch.float32, non_blocking=True)
-
-    xd, yd, zd, qxd, qyd = (to_dev(a) for a in (x, y, z, qx, qy))
-    g = aidw_grid_build(xd, yd, zd, params, stream)
-    try:
-        zq, _ = aidw_interpolate(g, qxd, qyd, params, stream=stream)
-        out = zq.to("cpu")
-    finally:
-        g.destroy()
-    return out
+    def host(a, name):
+        t = a if isinstance(a, torch.Tensor) else torch.from_numpy(np.ascontiguousarray(a))
+        if t.is_cuda or t.dtype != torch.float32 or t.dim() != 1 or not t.is_contiguous():
+            raise TypeError(f"{name} must be a contiguous 1-D float32 host array")
+        return t
+    x, y, z, qx, qy = (host(a, n) for a, n in ((x, "x"), (y, "y"), (z, "z"), (qx, "qx"),
+                                               (qy, "qy")))
+    if not (x.numel() == y.numel() == z.numel()) or qx.numel() != qy.numel():
+        raise ValueError("x, y, z (and qx, qy) must have the same length")
+    dt = torch.float64 if p.precision == AIDW_FP64_PLAIN else torch.float32
+    m = qx.numel()
+    out = torch.empty(m, dtype=dt, pin_memory=True)
+    alpha = torch.empty(m, dtype=dt, pin_memory=True) if want_alpha else None
+    pc = p.to_c()
+    _check(load().aidw_interpolate_host(_ptr(x), _ptr(y), _ptr(z), x.numel(), _ptr(qx),
+                                        _ptr(qy), m, ctypes.byref(pc), _ptr(out), _ptr(alpha),
+                                        _stream(stream)), "aidw_interpolate_host")
+    return (out, alpha) if want_alpha else out

@@ -176,12 +176,18 @@ int weight_resident_ctas(int device, bool fp64);
 
 // Batched weighting + finalize over jobs[0, n_jobs) (device array), total_u
 // units and total_q queries; part holds (total tiles + G) * query-tile
-// partial records; fail is one int of device memory for the launch's
-// failure flag (zeroed by the launch; a CTA whose wait expires sets it and
-// the finalize then writes NaN).
+// partial records; bounds (device, G + 1 entries, strictly increasing from
+// 0 to total_u; or null for equal unit counts) is the first unit of each
+// CTA's share; fail is one int of device memory for the launch's failure
+// flag (zeroed by the launch; a CTA whose wait expires sets it and the
+// finalize then writes NaN).
 aidw_status weight_launch_batch(const WJob *jobs, int n_jobs, long long total_u,
                                 long long total_q, bool fp64, void *part, long long G,
-                                int *status, int *fail, int device, cudaStream_t s);
+                                const long long *bounds, int *status, int *fail, int device,
+                                cudaStream_t s);
+// Points of data tile d that the weighting kernel processes for a job of
+// n_data points (n_pad padded): the cost of one unit.
+long long weight_unit_points(long long n_data, long long n_pad, long long d, bool fp64);
 size_t weight_partial_bytes(bool fp64);  // bytes of one query tile's partials
 // Instruction mix of the float32 weighting loop (see aidw_weight_mix).
 void weight_mix(int *products, int *poly_exp2, int *poly_lg2, double *fma_lanes, double *instr);

@@ -467,6 +467,54 @@ aidw_status aidw_interpolate_local(const aidw_grid *g, const float *qx, const fl
                       reinterpret_cast<cudaStream_t>(stream), out_z);
 }
 
+aidw_status aidw_interpolate_host(const float *x, const float *y, const float *z, int64_t n_data,
+                                  const float *qx, const float *qy, int64_t n_query,
+                                  const aidw_params *p, void *out_z, void *out_alpha,
+                                  aidw_stream_t stream)
+{
+    if (!x || !y || !z || n_data < 1 || n_data > kMaxPoints) return AIDW_ERR_INVALID_ARG;
+    if (n_query < 0 || n_query > kMaxPoints) return AIDW_ERR_INVALID_ARG;
+    aidw_status st = check_params(p, true);
+    if (st != AIDW_OK) return st;
+    if (p->k > n_data) return AIDW_ERR_K_RANGE;
+    if (n_query > 0 && (!qx || !qy || !out_z)) return AIDW_ERR_INVALID_ARG;
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    const size_t n = (size_t)n_data, m = (size_t)n_query;
+    const size_t es = p->precision == AIDW_FP64_PLAIN ? sizeof(double) : sizeof(float);
+    // one pool block: inputs (x, y, z, qx, qy), then the outputs 8-byte aligned
+    const size_t in_bytes = sizeof(float) * (3 * n + 2 * m);
+    const size_t out_off = (in_bytes + 255) / 256 * 256;
+    const size_t out_bytes = es * m * (out_alpha ? 2 : 1);
+    unsigned char *d = nullptr;
+    if (lib_alloc((void **)&d, out_off + out_bytes, s) != cudaSuccess) return AIDW_ERR_OOM;
+    float *dx = reinterpret_cast<float *>(d), *dy = dx + n, *dz = dy + n, *dqx = dz + n,
+          *dqy = dqx + m;
+    void *dout = d + out_off;
+    void *dalpha = out_alpha ? d + out_off + es * m : nullptr;
+    cudaError_t e = cudaMemcpyAsync(dx, x, sizeof(float) * n, cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(dy, y, sizeof(float) * n, cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(dz, z, sizeof(float) * n, cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess && m)
+        e = cudaMemcpyAsync(dqx, qx, sizeof(float) * m, cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess && m)
+        e = cudaMemcpyAsync(dqy, qy, sizeof(float) * m, cudaMemcpyHostToDevice, s);
+    st = cuda_status(e);
+    aidw_grid *g = nullptr;
+    if (st == AIDW_OK) st = aidw_grid_build(dx, dy, dz, n_data, p, stream, &g);
+    if (st == AIDW_OK && m) st = aidw_interpolate(g, dqx, dqy, n_query, p, dout, dalpha, stream);
+    if (st == AIDW_OK && m)
+        st = cuda_status(cudaMemcpyAsync(out_z, dout, es * m, cudaMemcpyDeviceToHost, s));
+    if (st == AIDW_OK && m && out_alpha)
+        st = cuda_status(cudaMemcpyAsync(out_alpha, dalpha, es * m, cudaMemcpyDeviceToHost, s));
+    if (st == AIDW_OK) st = cuda_status(cudaStreamSynchronize(s));
+    if (g) {
+        const aidw_status gs = aidw_grid_destroy(g);  // latched device errors of the call
+        if (st == AIDW_OK) st = gs;
+    }
+    lib_free(d, s);
+    return st;
+}
+
 aidw_status aidw_shard_range(int64_t n_query, int shard, int n_shards, int64_t *begin,
                              int64_t *end)
 {

@@ -14,6 +14,7 @@
 #include <string.h>
 
 #include <math.h>
+#include <stdio.h>
 #include <stdlib.h>
 
 #include <algorithm>
@@ -253,6 +254,7 @@ struct aidw_batch_plan {
     GridDev *d_grids = nullptr;
     int *d_status = nullptr;
     void *d_part = nullptr;
+    long long *d_bounds = nullptr;  // [G + 1] cost-balanced stream-K shares
 
     unsigned char *h_stage = nullptr;  // pinned copy of the three tables
     size_t stage_bytes = 0;
@@ -392,7 +394,7 @@ aidw_status enqueue(aidw_batch_plan *P, cudaStream_t s, bool knn_only)
     }
     if (st != AIDW_OK || knn_only) return st;
     st = weight_launch_batch(P->d_wj, J, P->total_u, P->total_q, P->fp64, P->d_part, P->G,
-                             P->d_status, P->d_status + 1, P->device, s);
+                             P->d_bounds, P->d_status, P->d_status + 1, P->device, s);
     if (st != AIDW_OK) return st;
     k_b_status<<<jb, 128, 0, s>>>(P->d_bj, J, P->d_status);
     return cuda_status(cudaGetLastError());
@@ -438,8 +440,10 @@ aidw_status check_jobs(const aidw_batch_plan *P, const aidw_job *jobs, int n_job
 // histogram of the jobs' shapes (log2 buckets of n and m, and k).  A plan
 // created for jobs with a cached key starts with that tuning.  With
 // AIDW_TUNE_CACHE=<file> the entries are also read from and appended to that
-// file (one line per entry: key, tab, the per-class scales and block sizes
-// and the measured build + kNN milliseconds), so later processes reuse them.
+// file, one JSON object per line:
+//   {"key": "...", "cell_scale": [s8, s16, s24, s32],
+//    "knn_threads": [t8, t16, t24, t32], "build_knn_ms": ms}
+// so later processes reuse them (a later line for the same key wins).
 struct TuneVal {
     double scale[kClasses];
     int threads[kClasses];
@@ -476,15 +480,18 @@ void cache_load_file()
     std::ifstream f(path);
     std::string line;
     while (std::getline(f, line)) {
-        const size_t tab = line.find('\t');
-        if (tab == std::string::npos) continue;
-        std::istringstream in(line.substr(tab + 1));
+        // the fixed shape written by cache_store; anything else is skipped
+        const std::string k0 = "{\"key\": \"";
+        if (line.compare(0, k0.size(), k0) != 0) continue;
+        const size_t kend = line.find('"', k0.size());
+        if (kend == std::string::npos) continue;
         TuneVal v;
-        bool ok = true;
-        for (int c = 0; c < kClasses; ++c) ok = ok && (in >> v.scale[c]);
-        for (int c = 0; c < kClasses; ++c) ok = ok && (in >> v.threads[c]);
-        ok = ok && (in >> v.ms);
-        if (ok) g_cache[line.substr(0, tab)] = v;
+        const int got = sscanf(line.c_str() + kend,
+                               "\", \"cell_scale\": [%lf, %lf, %lf, %lf], "
+                               "\"knn_threads\": [%d, %d, %d, %d], \"build_knn_ms\": %lf}",
+                               &v.scale[0], &v.scale[1], &v.scale[2], &v.scale[3],
+                               &v.threads[0], &v.threads[1], &v.threads[2], &v.threads[3], &v.ms);
+        if (got == 9) g_cache[line.substr(k0.size(), kend - k0.size())] = v;
     }
 }
 
@@ -516,11 +523,70 @@ void cache_store(const aidw_batch_plan *P, double ms)
     g_cache[key] = v;
     const char *path = getenv("AIDW_TUNE_CACHE");
     if (!path || !*path) return;
+    char buf[256];
+    snprintf(buf, sizeof buf,
+             "\", \"cell_scale\": [%.17g, %.17g, %.17g, %.17g], \"knn_threads\": [%d, %d, %d, %d], "
+             "\"build_knn_ms\": %.6g}\n",
+             v.scale[0], v.scale[1], v.scale[2], v.scale[3], v.threads[0], v.threads[1],
+             v.threads[2], v.threads[3], v.ms);
     std::ofstream f(path, std::ios::app);
-    f << key << '\t';
-    for (int c = 0; c < kClasses; ++c) f << v.scale[c] << ' ';
-    for (int c = 0; c < kClasses; ++c) f << v.threads[c] << ' ';
-    f << v.ms << '\n';
+    f << "{\"key\": \"" << key << buf;
+}
+
+// Cost-balanced stream-K shares of the weighting launch.  The units of all
+// jobs, in launch order, are split into G contiguous shares of about equal
+// cost, where a unit costs the points it processes (its data tile, part-filled
+// at a job's edge) plus a fixed overhead, and the first unit of a query-tile
+// row (a new segment: job look-up, query loads) a little more.  Equal unit
+// counts left the CTAs whose shares hold many small jobs' part-filled tiles
+// idle at the end (measured on the 512-job workload: per-SM active cycles,
+// max / mean 1.0074).  Shares are kept non-empty (strictly increasing
+// boundaries), which the partial-sum slots (tile + CTA) rely on.
+void stream_k_bounds(const aidw_batch_plan *P, std::vector<long long> &b)
+{
+    constexpr double kUnitCost = 16.0, kSegmentCost = 16.0;  // in points
+    const long long G = P->G, U = P->total_u;
+    b.assign((size_t)G + 1, 0);
+    b[(size_t)G] = U;
+    if (U <= G) {
+        for (long long k = 0; k < G; ++k) b[(size_t)k] = std::min(k, U);
+        return;
+    }
+    const int J = P->n_jobs;
+    std::vector<double> row(J, 0.0);
+    double total = 0.0;
+    for (int j = 0; j < J; ++j) {
+        const WJob &w = P->wj[j];
+        double r = kSegmentCost;
+        for (long long d = 0; d < w.D; ++d)
+            r += (double)weight_unit_points(w.n_data, w.n_pad, d, P->fp64) + kUnitCost;
+        row[j] = r;
+        total += (double)w.T * r;
+    }
+    long long k = 1;
+    double base = 0.0;
+    for (int j = 0; j < J && k < G; ++j) {
+        const WJob &w = P->wj[j];
+        const double jc = (double)w.T * row[j];
+        while (k < G && base + jc >= (double)k * total / (double)G) {
+            const double x = (double)k * total / (double)G - base;
+            long long t = std::min<long long>(w.T - 1, (long long)(x / row[j]));
+            double rem = x - (double)t * row[j] - kSegmentCost;
+            long long d = 0;
+            while (d < w.D - 1) {
+                const double c = (double)weight_unit_points(w.n_data, w.n_pad, d, P->fp64) + kUnitCost;
+                if (rem < c) break;
+                rem -= c;
+                ++d;
+            }
+            b[(size_t)k] = w.unit_base + t * w.D + d;
+            ++k;
+        }
+        base += jc;
+    }
+    for (; k < G; ++k) b[(size_t)k] = U;
+    for (long long i = 1; i < G; ++i) b[(size_t)i] = std::max(b[(size_t)i], b[(size_t)i - 1] + 1);
+    for (long long i = G - 1; i >= 1; --i) b[(size_t)i] = std::min(b[(size_t)i], b[(size_t)i + 1] - 1);
 }
 
 void free_plan(aidw_batch_plan *P)
@@ -663,6 +729,7 @@ aidw_status aidw_batch_plan_create(const aidw_job *jobs, int n_jobs, const aidw_
     const size_t o_startreg = take(sizeof(int) * (size_t)start_ints);
     const size_t o_qcountreg = take(sizeof(int) * (size_t)start_ints);
     const size_t o_part = take(weight_partial_bytes(P->fp64) * (size_t)(P->total_tiles + P->G));
+    const size_t o_bounds = take(sizeof(long long) * (size_t)(P->G + 1));
     const size_t o_tables = take((sizeof(BJob) + sizeof(KnnJob) + sizeof(WJob)) * (size_t)n_jobs);
     const size_t o_status = take(2 * sizeof(int));  // latched status, launch failure flag
     P->pool_bytes = off;
@@ -687,6 +754,7 @@ aidw_status aidw_batch_plan_create(const aidw_job *jobs, int n_jobs, const aidw_
     P->start_pool = reinterpret_cast<int *>(base + o_startreg);
     P->qcount_pool = reinterpret_cast<int *>(base + o_qcountreg);
     P->d_part = base + o_part;
+    P->d_bounds = reinterpret_cast<long long *>(base + o_bounds);
     P->d_bj = reinterpret_cast<BJob *>(base + o_tables);
     P->d_kj = reinterpret_cast<KnnJob *>(base + o_tables + sizeof(BJob) * n_jobs);
     P->d_wj = reinterpret_cast<WJob *>(base + o_tables + (sizeof(BJob) + sizeof(KnnJob)) * n_jobs);
@@ -745,6 +813,17 @@ aidw_status aidw_batch_plan_create(const aidw_job *jobs, int n_jobs, const aidw_
         memset(&kj, 0, sizeof(kj));
         P->kj.push_back(kj);
         P->korder.push_back(0);
+    }
+    {
+        std::vector<long long> bounds;
+        stream_k_bounds(P, bounds);
+        e = cudaMemcpy(P->d_bounds, bounds.data(), sizeof(long long) * bounds.size(),
+                       cudaMemcpyHostToDevice);
+        if (e != cudaSuccess) {
+            cudaGetLastError();
+            free_plan(P);
+            return AIDW_ERR_CUDA;
+        }
     }
     // a tuning measured earlier for jobs of the same shapes
     if (cache_lookup(P)) {

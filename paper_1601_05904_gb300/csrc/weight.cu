@@ -105,6 +105,9 @@ struct SKArgs {
     int n_jobs;
     long long U;        // units of all jobs
     long long G;        // CTAs
+    const long long *bounds;  // [G + 1] first unit of each CTA's share, strictly
+                              // increasing (cost-balanced, batched launches); or
+                              // null for equal unit counts
     long long total_q;  // queries of all jobs
     int *status;
     int *fail;          // this launch's failure flag: zeroed before the launch, set by a
@@ -113,6 +116,25 @@ struct SKArgs {
     long long skip_unit;  // test hook: the data tile of this unit is never
                           // copied, so its wait expires (-1: none)
 };
+
+// Share of CTA j and the owner of unit u, from the launch's boundaries.
+__device__ __forceinline__ long long share_begin(const SKArgs &a, long long j)
+{
+    return a.bounds ? a.bounds[j] : sk_begin(j, a.U, a.G);
+}
+__device__ __forceinline__ long long share_owner(const SKArgs &a, long long u)
+{
+    if (!a.bounds) return sk_owner(u, a.U, a.G);
+    long long lo = 0, hi = a.G - 1;  // the last CTA whose share starts at or before u
+    while (lo < hi) {
+        const long long mid = (lo + hi + 1) >> 1;
+        if (a.bounds[mid] <= u)
+            lo = mid;
+        else
+            hi = mid - 1;
+    }
+    return lo;
+}
 
 __device__ __forceinline__ WJob job_of_unit(const SKArgs &a, long long u)
 {
@@ -210,7 +232,7 @@ __global__ void __launch_bounds__(THREADS, MINB)
     __shared__ __align__(8) uint64_t full[kStages];
 
     const long long cta = blockIdx.x;
-    const long long u0 = sk_begin(cta, a.U, a.G), u1 = sk_begin(cta + 1, a.U, a.G);
+    const long long u0 = share_begin(a, cta), u1 = share_begin(a, cta + 1);
     if (u0 >= u1) return;
     if (threadIdx.x == 0) {
         for (int s = 0; s < kStages; ++s) mbar_init(&full[s], 1);
@@ -366,7 +388,7 @@ __global__ void k_finalize_f32(SKArgs a, const float4 *__restrict__ part)
     }
     const long long t = q / C::kQTile, l = q % C::kQTile;
     const long long ub = J.unit_base + t * J.D;
-    const long long j0 = sk_owner(ub, a.U, a.G), j1 = sk_owner(ub + J.D - 1, a.U, a.G);
+    const long long j0 = share_owner(a, ub), j1 = share_owner(a, ub + J.D - 1);
     float hw = 0.0f, lw = 0.0f, hz = 0.0f, lz = 0.0f;
     for (long long j = j0; j <= j1; ++j) {
         const float4 v = part[(J.tile_base + t + j) * C::kQTile + l];
@@ -392,7 +414,7 @@ __global__ void __launch_bounds__(WCfg<true>::kThreads, WCfg<true>::kMinBlocks)
     __shared__ __align__(8) uint64_t full[kStages];
 
     const long long cta = blockIdx.x;
-    const long long u0 = sk_begin(cta, a.U, a.G), u1 = sk_begin(cta + 1, a.U, a.G);
+    const long long u0 = share_begin(a, cta), u1 = share_begin(a, cta + 1);
     if (u0 >= u1) return;
     if (threadIdx.x == 0) {
         for (int s = 0; s < kStages; ++s) mbar_init(&full[s], 1);
@@ -483,7 +505,7 @@ __global__ void k_finalize_f64(SKArgs a, const double2 *__restrict__ part)
     }
     const long long t = q / C::kQTile, l = q % C::kQTile;
     const long long ub = J.unit_base + t * J.D;
-    const long long j0 = sk_owner(ub, a.U, a.G), j1 = sk_owner(ub + J.D - 1, a.U, a.G);
+    const long long j0 = share_owner(a, ub), j1 = share_owner(a, ub + J.D - 1);
     double sw = 0.0, swz = 0.0;
     for (long long j = j0; j <= j1; ++j) {
         const double2 v = part[(J.tile_base + t + j) * C::kQTile + l];
@@ -715,6 +737,13 @@ void weight_expire_next_wait(int tries)
     g_hook_tries = tries;
 }
 
+long long weight_unit_points(long long n_data, long long n_pad, long long d, bool fp64)
+{
+    if (fp64) return std::min<long long>(kDTile, n_pad - d * kDTile);
+    const long long rem = n_data - d * kDTile;
+    return std::min<long long>(kDTile, (rem + kChunk2 - 1) / kChunk2 * kChunk2);
+}
+
 long long weight_data_tiles(long long n_data, long long n_pad, bool fp64)
 {
     return fp64 ? (n_pad + kDTile - 1) / kDTile : (n_data + kDTile - 1) / kDTile;
@@ -756,7 +785,8 @@ aidw_status weight_launch(const aidw_grid *g, const float *qx, const float *qy,
 
 aidw_status weight_launch_batch(const WJob *jobs, int n_jobs, long long total_u,
                                 long long total_q, bool fp64, void *part, long long G,
-                                int *status, int *fail, int device, cudaStream_t s)
+                                const long long *bounds, int *status, int *fail, int device,
+                                cudaStream_t s)
 {
     if (total_u <= 0 || total_q <= 0) return AIDW_OK;
     SKArgs a;
@@ -765,6 +795,7 @@ aidw_status weight_launch_batch(const WJob *jobs, int n_jobs, long long total_u,
     a.n_jobs = n_jobs;
     a.U = total_u;
     a.G = std::max<long long>(1, std::min<long long>(G, total_u));
+    a.bounds = a.G == G ? bounds : nullptr;
     a.total_q = total_q;
     a.status = status;
     a.fail = fail;

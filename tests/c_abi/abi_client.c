@@ -1,7 +1,8 @@
 /* A plain C client of the library: reads float32 inputs from a directory,
- * runs the grid build, kNN, interpolation (both precisions), the local form
- * and a two-job batch through include/aidw.h with device memory from the
- * CUDA runtime, and writes the outputs next to the inputs.  Used by
+ * runs the grid build, kNN, interpolation (both precisions), the local form,
+ * a two-job batch and the end-to-end call from host arrays through
+ * include/aidw.h with device memory from the CUDA runtime, and writes the
+ * outputs next to the inputs.  Used by
  * tests/test_gpu_c_abi.py; no Python or torch is involved in the calls. */
 #include <stdint.h>
 #include <stdio.h>
@@ -133,6 +134,10 @@ int main(int argc, char **argv)
     CHECK(aidw_batch(jobs, 2, &p, NULL));
     if (cudaDeviceSynchronize() != cudaSuccess) return 3;
 
+    /* end to end from the host arrays */
+    float *hz32 = (float *)malloc(4 * (size_t)m), *ha32 = (float *)malloc(4 * (size_t)m);
+    CHECK(aidw_interpolate_host(hx, hy, hz, n, hqx, hqy, m, &p, hz32, ha32, NULL));
+
     int rc = 0;
     rc |= fetch(dir, "z32.bin", z32, 4 * (size_t)m);
     rc |= fetch(dir, "alpha32.bin", a32, 4 * (size_t)m);
@@ -143,6 +148,8 @@ int main(int argc, char **argv)
     rc |= fetch(dir, "robs.bin", robs, 4 * (size_t)m);
     rc |= fetch(dir, "zbatch0.bin", zb0, 4 * (size_t)m);
     rc |= fetch(dir, "zbatch1.bin", zb1, 4 * (size_t)m);
+    rc |= write_bytes(dir, "zhost.bin", hz32, 4 * (size_t)m);
+    rc |= write_bytes(dir, "alphahost.bin", ha32, 4 * (size_t)m);
     printf("ok n_col=%lld n_row=%lld cell_width=%.9g\n", (long long)info.n_col,
            (long long)info.n_row, info.cell_width);
     return rc;

@@ -141,3 +141,20 @@ def test_shard_range_rejects_bad_shards(lib):
     for n, r, w in ((-1, 0, 1), (10, 1, 1), (10, -1, 2), (10, 0, 0)):
         assert lib.aidw_shard_range(n, r, w, ctypes.byref(b), ctypes.byref(e)) == 1
     assert lib.aidw_shard_range(10, 0, 1, None, ctypes.byref(e)) == 1
+
+
+def test_host_entry_point_checks_arguments_without_a_gpu(lib):
+    """aidw_interpolate_host rejects bad arguments before any CUDA call."""
+    from paper_1601_05904_gb300 import binding
+    pc = _params(k=2)
+    a = (ctypes.c_float * 4)()
+    out = (ctypes.c_float * 4)()
+    f = lib.aidw_interpolate_host
+    assert f(None, a, a, 4, a, a, 4, ctypes.byref(pc), out, None, None) == 1
+    assert f(a, a, a, 0, a, a, 4, ctypes.byref(pc), out, None, None) == 1
+    assert f(a, a, a, 4, None, a, 4, ctypes.byref(pc), out, None, None) == 1
+    assert f(a, a, a, 4, a, a, 4, ctypes.byref(pc), None, None, None) == 1
+    assert f(a, a, a, 4, a, a, -1, ctypes.byref(pc), out, None, None) == 1
+    p5 = _params(k=5)
+    assert f(a, a, a, 4, a, a, 4, ctypes.byref(p5), out, None, None) == 2   # k > n_data
+    del binding

@@ -223,7 +223,11 @@ def test_tuning_cache_file_reaches_a_new_process(tmp_path):
         return json.loads(r.stdout.strip().splitlines()[-1])
     first = run("tune")
     assert first["source"] == "tuner"
-    assert (tmp_path / "tune.txt").read_text().count("\n") == 1
+    lines = (tmp_path / "tune.txt").read_text().splitlines()
+    assert len(lines) == 1
+    entry = json.loads(lines[0])        # one JSON object per line
+    assert entry["cell_scale"] == [c["cell_scale"] for c in first["classes"]]
+    assert entry["knn_threads"] == [c["knn_threads"] for c in first["classes"]]
     second = run("create")
     assert second["source"] == "cache"
     assert second["classes"] == first["classes"]

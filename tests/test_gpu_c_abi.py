@@ -56,6 +56,10 @@ def test_c_client_matches_the_oracle(client, oracle, tmp_path):
         err = oracle.normalized_error(load(name, dt), ref["z"], ref["scale"])
         assert err.max() <= tol, (name, err.max())
     np.testing.assert_allclose(load("alpha32.bin", np.float32), ref["alpha"], atol=1e-5)
+    # the end-to-end call from host arrays runs the same kernels
+    np.testing.assert_array_equal(load("zhost.bin", np.float32), load("z32.bin", np.float32))
+    np.testing.assert_array_equal(load("alphahost.bin", np.float32),
+                                  load("alpha32.bin", np.float32))
     ref4 = oracle.aidw(w.x, w.y, w.z, w.qx, w.qy, 4)
     assert oracle.normalized_error(load("zbatch1.bin", np.float32), ref4["z"],
                                    ref4["scale"]).max() <= TOL_FP32

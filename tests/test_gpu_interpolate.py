@@ -201,3 +201,26 @@ def test_precision_form_4M_sampled(aidw, oracle):
     s_abs, _ = _interp(aidw, w.x, w.y, np.abs(w.z), w.qx[:q], w.qy[:q], 10)
     err = np.abs(zq[:q].astype(np.float64) - z64) / s_abs.astype(np.float64)
     assert err.max() <= TOL_FP32, err.max()
+
+
+@pytest.mark.parametrize("fp64", [False, True])
+def test_interpolate_from_host_arrays(aidw, oracle, fp64):
+    """aidw_interpolate_host (copies in, grid build, interpolation, copies
+    out, all inside the library) gives exactly the device-array path's
+    predictions and alphas, from pageable numpy arrays and pinned tensors."""
+    import torch
+    w = inputs.clustered_kilo(n=15000, m=3000, k=12, seed=71)
+    p = aidw.Params(k=12, precision=aidw.AIDW_FP64_PLAIN if fp64 else aidw.AIDW_FP32_COMP)
+    g = aidw.aidw_grid_build(dev(w.x), dev(w.y), dev(w.z), p)
+    ref_z, ref_a = aidw.aidw_interpolate(g, dev(w.qx), dev(w.qy), p, want_alpha=True)
+    g.destroy()
+    z, a = aidw.interpolate_host(w.x, w.y, w.z, w.qx, w.qy, p, want_alpha=True)
+    np.testing.assert_array_equal(z.numpy(), host(ref_z))
+    np.testing.assert_array_equal(a.numpy(), host(ref_a))
+    pinned = [torch.from_numpy(getattr(w, k)).pin_memory() for k in ("x", "y", "z", "qx", "qy")]
+    z2 = aidw.interpolate_host(*pinned, p)
+    np.testing.assert_array_equal(z2.numpy(), host(ref_z))
+    ref = oracle.aidw(w.x, w.y, w.z, w.qx[:300], w.qy[:300], 12)
+    err = oracle.normalized_error(z.numpy()[:300], ref["z"], ref["scale"])
+    assert err.max() <= (TOL_FP64 if fp64 else TOL_FP32)
+    assert aidw.interpolate_host(w.x, w.y, w.z, w.qx[:0], w.qy[:0], p).numel() == 0
