@@ -191,8 +191,28 @@ __device__ __forceinline__ float decay_power_f32(float mu, const float (&a)[5])
     return a[4];
 }
 
+// Register budget of the float32 kNN kernel per top-k width: a minimum of
+// 2 resident blocks of 256 threads holds it to 128 registers.  Left free,
+// the compiler gives the 32/24/16/8-slot forms 174/164/148/128 registers.
+// Measured on GB300 at 1M (kNN ms incl. query order; free 32-slot form:
+// uniform k = 32 2.83): caps on (32, 24, 16, 8) = (2, 1, 1, 1): uniform
+// k = 10 0.666, clustered k = 8/10/24/32 0.939/1.189/2.279/2.671, uniform
+// k = 32 1.690, 512-job build + kNN 29.15; (2, 2, 1, 1): 0.667, 0.939/1.199/
+// 1.951/2.666, 1.690, 28.1; (2, 2, 2, 2): 0.546, 0.931/1.018/1.948/2.668,
+// 1.689, 26.9.  Three blocks (80 registers) spill.  The float64 path is
+// left free (capping its 32-slot form spills heavily).
+constexpr int kKnnMinBlocks32 = 2, kKnnMinBlocks24 = 2, kKnnMinBlocks16 = 2,
+              kKnnMinBlocks8 = 2;
+constexpr int knn_min_blocks(bool f64, int kmax)
+{
+    return f64 ? 1
+               : (kmax >= 32 ? kKnnMinBlocks32
+                             : (kmax >= 24 ? kKnnMinBlocks24
+                                           : (kmax >= 16 ? kKnnMinBlocks16 : kKnnMinBlocks8)));
+}
+
 template <bool F64, int KMAX>
-__global__ void __launch_bounds__(kKnnMaxThreads)
+__global__ void __launch_bounds__(kKnnMaxThreads, knn_min_blocks(F64, KMAX))
     k_knn(KnnJob job0, const KnnJob *__restrict__ jobs, int n_jobs, long long total_q,
           AlphaParams ap)
 {
@@ -270,8 +290,6 @@ __global__ void __launch_bounds__(kKnnMaxThreads)
     D kth = DistT<F64>::inf();
     int kthi = 0x7fffffff;
     long long found = 0;
-    int n_hit = 0;
-    HitSum<F64> hits;
     int L0 = -1;  // paper rule: the first level whose block holds k points
 
     for (int L = 0;; ++L) {
@@ -303,14 +321,17 @@ __global__ void __launch_bounds__(kKnnMaxThreads)
             const long long base = (long long)r * nc;
             const int a = start[base + ca], b = start[base + cb + 1];
             found += b - a;
+            // the next point's load is issued before the current one is
+            // tested, so its L2 latency overlaps the top-k update (kNN ms at
+            // 1M, uniform k = 10 / clustered k = 10, 24, 32: 0.545 / 1.011,
+            // 1.948, 2.668 -> 0.528 / 0.958, 1.818, 2.556)
+            const float4 *P4 = reinterpret_cast<const float4 *>(pts);
+            float4 nxt = a < b ? P4[a] : make_float4(0.0f, 0.0f, 0.0f, 0.0f);
             for (int s = a; s < b; ++s) {
-                const float4 p = reinterpret_cast<const float4 *>(pts)[s];
+                const float4 p = nxt;
+                if (s + 1 < b) nxt = P4[s + 1];
                 const int pidx = __float_as_int(p.w);
                 const D d2 = DistT<F64>::d2(qx, qy, p.x, p.y);
-                if (d2 == (D)0) {
-                    ++n_hit;
-                    hits.add(p.z);
-                }
                 if (d2 < kth || (d2 == kth && pidx < kthi)) {
                     // replace the k-th and bubble the candidate down to its
                     // place.  Once it stops, no later step swaps, so the exit
@@ -369,13 +390,37 @@ __global__ void __launch_bounds__(kKnnMaxThreads)
         r_obs = rf;
         alpha = decay_power_f32(membership_f32(rf, g, ap), ap.level_f);
     }
-    double hit_z = 0.0;
-    if (n_hit > 0) hit_z = hits.value() / (double)n_hit;
-
     D d1 = kd[KMAX - 1];  // the nearest, kd[lo]
 #pragma unroll
     for (int j = 0; j < KMAX - 1; ++j)
         if (j == lo) d1 = kd[j];
+
+    // Data points at distance 0 (the limit of Eq. 1 for a query on data):
+    // counted and their z summed by a second scan, only for a query whose
+    // nearest neighbour is at distance 0, instead of a test on every
+    // candidate of the search.  Such a point is within the underflow range
+    // of the squared distance of the query (|dx|, |dy| < 2^-63), so its cell
+    // index differs from the query's by at most ceil(2^-63 / cw) + 1 per
+    // axis (1 on any grid whose cells are wider than 2^-63).
+    int n_hit = 0;
+    double hit_z = 0.0;
+    if (d1 == (D)0) {
+        const double reach = 0x1p-63 / cw;
+        const int R = reach < 1.0 ? 1 : (int)fmin(ceil(reach) + 1.0, (double)max(nc, nr));
+        HitSum<F64> hits;
+        for (int r = max(row - R, 0); r <= min(row + R, nr - 1); ++r) {
+            const long long base = (long long)r * nc;
+            const int a = start[base + max(col - R, 0)], b = start[base + min(col + R, nc - 1) + 1];
+            for (int s = a; s < b; ++s) {
+                const float4 p = reinterpret_cast<const float4 *>(pts)[s];
+                if (DistT<F64>::d2(qx, qy, p.x, p.y) == (D)0) {
+                    ++n_hit;
+                    hits.add(p.z);
+                }
+            }
+        }
+        hit_z = hits.value() / (double)n_hit;
+    }
     if (recs) {
         QRec r;
         r.alpha = alpha;
