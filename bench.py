@@ -616,6 +616,7 @@ def batch_measure(ctx, n_jobs, steps, warmup, tune, seed_base=1000, clocks=None,
     tune_ms = binding.aidw_batch_plan_tune(plan, jobs) if tune else None
     tune_s = time.perf_counter() - t0
     info = binding.aidw_batch_plan_get(plan)
+    info["classes"] = binding.aidw_batch_plan_get_classes(plan)
     ms, _, clk = ctx.time_steps(lambda: binding.aidw_batch_run(plan, jobs), steps, warmup,
                                 clocks)
     if binding.aidw_batch_plan_status(plan) != 0:
