@@ -319,9 +319,10 @@ def stage_rooflines(stage, n_data, n_query, n_cells, hbm_gbs):
         out["knn"] = {"bound": "hbm", "achieved": ach, "peak": hbm_gbs, "unit": "GB/s",
                       "frac": ach / hbm_gbs, "ms": k_ms, "algorithmic_bytes": by,
                       "launches": k_l,
-                      "note": "bound by dependent L2 gathers of the ring search and the "
-                              "register top-k, not by HBM: the cell-ordered points "
-                              "(16 B each) stay in L2 at these sizes"}
+                      "note": "bound by the SM (dependent gathers of the ring search, "
+                              "mostly L1 hits, and the register top-k), not by memory: "
+                              "ncu at 1M puts k_knn at 54 % of SM throughput, 3.5 % of "
+                              "L2 and 0.9 % of DRAM throughput"}
     return out
 
 
