@@ -890,9 +890,9 @@ def run_batch(args):
 
 
 # DRAM bytes (read + write) of one k_weight_f32 launch per data point, from
-# the ncu capture at n = m = 131,072 (5.83 MB read, 0 written); every input
+# the ncu capture at n = m = 131,072 (5.82 MB read, 0 written); every input
 # (points, queries, kNN records) is read once, so it scales with n = m.
-WEIGHT_DRAM_BYTES_PER_POINT = 5.825536e6 / 131072
+WEIGHT_DRAM_BYTES_PER_POINT = 5.821696e6 / 131072
 
 
 def _time_ms(fn, reps):
