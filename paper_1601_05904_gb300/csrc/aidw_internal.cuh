@@ -12,8 +12,8 @@ namespace aidw {
 // Device-side description of a built grid (one per grid, in device memory).
 // ---------------------------------------------------------------------------
 struct GridDev {
-    // bounding box as order-preserving integer encodings of float32, updated
-    // with atomicMin/atomicMax during the reduction
+    // bounding box as order-preserving integer encodings of float32 (written
+    // by the last block of the bounding-box reduction)
     int enc_min_x, enc_min_y, enc_max_x, enc_max_y;
     double min_x, min_y, max_x, max_y;
     double area;        // A of Eq. 2

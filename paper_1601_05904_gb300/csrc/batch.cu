@@ -4,7 +4,10 @@
 // A plan fixes the job shapes (n_data, n_query, k per job) and carves one
 // pooled device allocation into every job's grid arrays, kNN records and the
 // weighting partial sums.  Each step of the path is one launch over all jobs:
-// the grid-build kernels map blocks to jobs through per-job block prefixes,
+// the grid-build kernels (the single-grid build's five: bounding box with the
+// dimensions from its last block, keys, single-pass scan, scatter, fix-up
+// with padding; each job has its own tickets and scan records) map blocks
+// to jobs through per-job block prefixes,
 // the kNN kernels (one per top-k width class) map queries to jobs, and the
 // weighting stage is a single persistent stream-K launch over the units of
 // all jobs, so jobs of very different sizes share the GPU evenly.  The launch
@@ -45,16 +48,23 @@ struct BJob {
     int *perm;
     float *wt;
     int *key, *rank, *tmp;
-    int *bsum;
+    float *bpart;                      // bounding-box records, 5 per block
+    // zeroed at the start of every run, after the cell heads in the start
+    // region: the scan's chunk records and the tickets (bounding box, scan)
+    unsigned long long *flags;
+    int *tickets;
     long long n, n_pad, n_wpad, cap;
     long long nchunks;      // scan chunks of start[0, cap]
     long long bbox_blocks;  // blocks of the bounding-box reduction
-    long long blk_pt, blk_bbox, blk_scan, blk_pad;  // first block in each launch
+    long long blk_pt, blk_bbox, blk_scan, blk_fp;  // first block in each launch
     double cell_scale, area_param;
-    // queries, sorted by grid cell before the kNN (see knn.cu)
+    // queries, sorted by grid cell before the kNN (see knn.cu); qflags and
+    // qticket follow the counts in the query-count region
     const float *qx, *qy;
     long long m;
     int *qcount, *qkey, *qrank, *qorder;
+    unsigned long long *qflags;
+    int *qticket;
     long long blk_q;
 };
 
@@ -73,23 +83,12 @@ __device__ __forceinline__ int job_of_block(const BJob *__restrict__ jobs, int n
     return lo;
 }
 
-__global__ void k_b_init(const BJob *__restrict__ jobs, int n_jobs)
-{
-    const int j = blockIdx.x * blockDim.x + threadIdx.x;
-    if (j < n_jobs) grid_init(jobs[j].g, jobs[j].n);
-}
-
-__global__ void __launch_bounds__(kThreads) k_b_bbox(const BJob *__restrict__ jobs, int n_jobs)
+__global__ void __launch_bounds__(kThreads) k_b_bbox_dims(const BJob *__restrict__ jobs,
+                                                          int n_jobs)
 {
     const BJob &J = jobs[job_of_block<&BJob::blk_bbox>(jobs, n_jobs, blockIdx.x)];
-    const long long lb = blockIdx.x - J.blk_bbox;
-    bbox_block(J.x, J.y, J.z, lb * kThreads + threadIdx.x, J.n, J.bbox_blocks * kThreads, J.g);
-}
-
-__global__ void k_b_dims(const BJob *__restrict__ jobs, int n_jobs)
-{
-    const int j = blockIdx.x * blockDim.x + threadIdx.x;
-    if (j < n_jobs) grid_dims(jobs[j].g, jobs[j].cell_scale, jobs[j].area_param, jobs[j].cap);
+    bbox_dims_block(J.x, J.y, J.z, J.n, J.bpart, J.tickets, J.g, J.cell_scale, J.area_param, J.cap,
+                    blockIdx.x - J.blk_bbox, J.bbox_blocks);
 }
 
 __global__ void __launch_bounds__(kThreads) k_b_keys(const BJob *__restrict__ jobs, int n_jobs)
@@ -100,26 +99,12 @@ __global__ void __launch_bounds__(kThreads) k_b_keys(const BJob *__restrict__ jo
     key_one(i, J.x, J.y, J.g, J.start, J.key, J.rank);
 }
 
-__global__ void __launch_bounds__(kThreads) k_b_scan_reduce(const BJob *__restrict__ jobs,
-                                                            int n_jobs)
+// One chunk of one job's single-pass scan; the chunk comes from the job's
+// own ticket, so a block waits only on earlier chunks of its job.
+__global__ void __launch_bounds__(kThreads) k_b_scan(const BJob *__restrict__ jobs, int n_jobs)
 {
     const BJob &J = jobs[job_of_block<&BJob::blk_scan>(jobs, n_jobs, blockIdx.x)];
-    const long long c = blockIdx.x - J.blk_scan;
-    scan_reduce_chunk(J.start, J.cap + 1, c, J.bsum + c);
-}
-
-__global__ void __launch_bounds__(kThreads) k_b_scan_sums(const BJob *__restrict__ jobs)
-{
-    const BJob &J = jobs[blockIdx.x];
-    scan_sums(J.bsum, (int)J.nchunks);
-}
-
-__global__ void __launch_bounds__(kThreads) k_b_scan_apply(const BJob *__restrict__ jobs,
-                                                           int n_jobs)
-{
-    const BJob &J = jobs[job_of_block<&BJob::blk_scan>(jobs, n_jobs, blockIdx.x)];
-    const long long c = blockIdx.x - J.blk_scan;
-    scan_apply_chunk(J.start, J.cap + 1, c, J.bsum[c]);
+    scan_lookback_block(J.start, J.cap + 1, J.flags, J.tickets + 1, &J.g->status);
 }
 
 __global__ void __launch_bounds__(kThreads) k_b_scatter(const BJob *__restrict__ jobs, int n_jobs)
@@ -130,19 +115,16 @@ __global__ void __launch_bounds__(kThreads) k_b_scatter(const BJob *__restrict__
     scatter_one(i, J.start, J.key, J.rank, J.tmp);
 }
 
-__global__ void __launch_bounds__(kThreads) k_b_fixup(const BJob *__restrict__ jobs, int n_jobs)
+__global__ void __launch_bounds__(kThreads) k_b_fixup_pad(const BJob *__restrict__ jobs,
+                                                          int n_jobs)
 {
-    const BJob &J = jobs[job_of_block<&BJob::blk_pt>(jobs, n_jobs, blockIdx.x)];
-    const long long s = (blockIdx.x - J.blk_pt) * kThreads + threadIdx.x;
-    if (s >= J.n || grid_failed(J.g)) return;
-    fixup_one(s, J.x, J.y, J.z, J.start, J.key, J.tmp, J.pts, J.perm, J.wt);
-}
-
-__global__ void __launch_bounds__(kThreads) k_b_pad(const BJob *__restrict__ jobs, int n_jobs)
-{
-    const BJob &J = jobs[job_of_block<&BJob::blk_pad>(jobs, n_jobs, blockIdx.x)];
-    const long long i = J.n + (blockIdx.x - J.blk_pad) * kThreads + threadIdx.x;
-    pad_one(i, J.n_pad, J.n_wpad, J.pts, J.wt);
+    const BJob &J = jobs[job_of_block<&BJob::blk_fp>(jobs, n_jobs, blockIdx.x)];
+    const long long s = (blockIdx.x - J.blk_fp) * kThreads + threadIdx.x;
+    if (s < J.n) {
+        if (!grid_failed(J.g)) fixup_one(s, J.x, J.y, J.z, J.start, J.key, J.tmp, J.pts, J.perm, J.wt);
+    } else if (s < (J.n_pad > J.n_wpad ? J.n_pad : J.n_wpad)) {
+        pad_one(s, J.n_pad, J.n_wpad, J.pts, J.wt);
+    }
 }
 
 // ---- queries of every job in grid-cell order (as the single-grid kNN) ----
@@ -156,26 +138,10 @@ __global__ void __launch_bounds__(kThreads) k_b_qkeys(const BJob *__restrict__ j
     key_one_xy(i, x, y, J.g, J.qcount, J.qkey, J.qrank);
 }
 
-__global__ void __launch_bounds__(kThreads) k_b_qscan_reduce(const BJob *__restrict__ jobs,
-                                                             int n_jobs)
+__global__ void __launch_bounds__(kThreads) k_b_qscan(const BJob *__restrict__ jobs, int n_jobs)
 {
     const BJob &J = jobs[job_of_block<&BJob::blk_scan>(jobs, n_jobs, blockIdx.x)];
-    const long long c = blockIdx.x - J.blk_scan;
-    scan_reduce_chunk(J.qcount, J.cap + 1, c, J.bsum + c);
-}
-
-__global__ void __launch_bounds__(kThreads) k_b_qscan_sums(const BJob *__restrict__ jobs)
-{
-    const BJob &J = jobs[blockIdx.x];
-    scan_sums(J.bsum, (int)J.nchunks);
-}
-
-__global__ void __launch_bounds__(kThreads) k_b_qscan_apply(const BJob *__restrict__ jobs,
-                                                            int n_jobs)
-{
-    const BJob &J = jobs[job_of_block<&BJob::blk_scan>(jobs, n_jobs, blockIdx.x)];
-    const long long c = blockIdx.x - J.blk_scan;
-    scan_apply_chunk(J.qcount, J.cap + 1, c, J.bsum[c]);
+    scan_lookback_block(J.qcount, J.cap + 1, J.qflags, J.qticket, &J.g->status);
 }
 
 __global__ void __launch_bounds__(kThreads) k_b_qscatter(const BJob *__restrict__ jobs, int n_jobs)
@@ -239,7 +205,7 @@ struct aidw_batch_plan {
     std::vector<int> korder;  // job index of each kj entry
     int kclass_begin[kClasses + 1] = {};
     long long kclass_q[kClasses] = {};
-    long long total_pt_blocks = 0, total_bbox_blocks = 0, total_chunks = 0, total_pad_blocks = 0;
+    long long total_pt_blocks = 0, total_bbox_blocks = 0, total_chunks = 0, total_fp_blocks = 0;
     long long total_q_blocks = 0;
     int *qcount_pool = nullptr;
     long long total_u = 0, total_q = 0, total_tiles = 0, G = 1;
@@ -343,25 +309,17 @@ aidw_status enqueue(aidw_batch_plan *P, cudaStream_t s, bool knn_only)
 {
     const int J = P->n_jobs;
     const unsigned jb = (unsigned)cdiv(J, 128);
-    k_b_init<<<jb, 128, 0, s>>>(P->d_bj, J);
-    k_b_bbox<<<(unsigned)P->total_bbox_blocks, kThreads, 0, s>>>(P->d_bj, J);
-    k_b_dims<<<jb, 128, 0, s>>>(P->d_bj, J);
+    // cell counts, scan records and tickets of every job start at zero
     cudaMemsetAsync(P->start_pool, 0, sizeof(int) * (size_t)P->start_ints, s);
+    k_b_bbox_dims<<<(unsigned)P->total_bbox_blocks, kThreads, 0, s>>>(P->d_bj, J);
     k_b_keys<<<(unsigned)P->total_pt_blocks, kThreads, 0, s>>>(P->d_bj, J);
-    k_b_scan_reduce<<<(unsigned)P->total_chunks, kThreads, 0, s>>>(P->d_bj, J);
-    k_b_scan_sums<<<(unsigned)J, kThreads, 0, s>>>(P->d_bj);
-    k_b_scan_apply<<<(unsigned)P->total_chunks, kThreads, 0, s>>>(P->d_bj, J);
+    k_b_scan<<<(unsigned)P->total_chunks, kThreads, 0, s>>>(P->d_bj, J);
     k_b_scatter<<<(unsigned)P->total_pt_blocks, kThreads, 0, s>>>(P->d_bj, J);
-    k_b_fixup<<<(unsigned)P->total_pt_blocks, kThreads, 0, s>>>(P->d_bj, J);
-    if (P->total_pad_blocks > 0)
-        k_b_pad<<<(unsigned)P->total_pad_blocks, kThreads, 0, s>>>(P->d_bj, J);
+    k_b_fixup_pad<<<(unsigned)P->total_fp_blocks, kThreads, 0, s>>>(P->d_bj, J);
     if (P->total_q_blocks > 0) {
-        // the data scan is complete, so its chunk sums (bsum) can be reused
         cudaMemsetAsync(P->qcount_pool, 0, sizeof(int) * (size_t)P->start_ints, s);
         k_b_qkeys<<<(unsigned)P->total_q_blocks, kThreads, 0, s>>>(P->d_bj, J);
-        k_b_qscan_reduce<<<(unsigned)P->total_chunks, kThreads, 0, s>>>(P->d_bj, J);
-        k_b_qscan_sums<<<(unsigned)J, kThreads, 0, s>>>(P->d_bj);
-        k_b_qscan_apply<<<(unsigned)P->total_chunks, kThreads, 0, s>>>(P->d_bj, J);
+        k_b_qscan<<<(unsigned)P->total_chunks, kThreads, 0, s>>>(P->d_bj, J);
         k_b_qscatter<<<(unsigned)P->total_q_blocks, kThreads, 0, s>>>(P->d_bj, J);
     }
     aidw_status st = cuda_status(cudaGetLastError());
@@ -652,7 +610,7 @@ aidw_status aidw_batch_plan_create(const aidw_job *jobs, int n_jobs, const aidw_
 
     // ---- sizes and block prefixes ----
     const long long qt = weight_query_tile(P->fp64);
-    long long blk_pt = 0, blk_bbox = 0, blk_pad = 0, ubase = 0, tbase = 0, qbase = 0;
+    long long blk_pt = 0, blk_bbox = 0, blk_fp = 0, ubase = 0, tbase = 0, qbase = 0;
     size_t off = 0;
     auto take = [&](size_t bytes) {
         const size_t o = off;
@@ -662,8 +620,11 @@ aidw_status aidw_batch_plan_create(const aidw_job *jobs, int n_jobs, const aidw_
     // the start region is sized for the smallest scale the tuner may pick
     const double scale_for_cap = P->tuned_scale ? p->cell_scale : kMinScale;
     std::vector<size_t> o_pts(n_jobs), o_wt(n_jobs), o_start(n_jobs), o_perm(n_jobs),
-        o_key(n_jobs), o_rank(n_jobs), o_tmp(n_jobs), o_bsum(n_jobs), o_rec(n_jobs),
+        o_key(n_jobs), o_rank(n_jobs), o_tmp(n_jobs), o_bpart(n_jobs), o_rec(n_jobs),
         o_qkey(n_jobs), o_qrank(n_jobs), o_qorder(n_jobs);
+    // inside each job's share of the start (and query-count) region, in ints:
+    // the cell heads, then the scan records, then the tickets
+    std::vector<long long> flags_off(n_jobs), tick_off(n_jobs);
     long long blk_q = 0;
     const size_t o_grids = take(sizeof(GridDev) * (size_t)n_jobs);
     long long start_ints = 0;
@@ -680,9 +641,8 @@ aidw_status aidw_batch_plan_create(const aidw_job *jobs, int n_jobs, const aidw_
         blk_pt += cdiv(b.n, kThreads);
         b.blk_bbox = blk_bbox;
         blk_bbox += b.bbox_blocks;
-        const long long pads = std::max(b.n_pad, b.n_wpad) - b.n;
-        b.blk_pad = blk_pad;
-        blk_pad += cdiv(pads, kThreads);
+        b.blk_fp = blk_fp;  // fix-up of the n points and the padding after them
+        blk_fp += cdiv(std::max(b.n, std::max(b.n_pad, b.n_wpad)), kThreads);
         const long long cap_max = grid_cells_capacity(b.n, scale_for_cap);
         o_pts[j] = take(sizeof(Point) * (size_t)b.n_pad);
         o_wt[j] = take(sizeof(float) * 3 * (size_t)b.n_wpad);
@@ -690,7 +650,7 @@ aidw_status aidw_batch_plan_create(const aidw_job *jobs, int n_jobs, const aidw_
         o_key[j] = take(sizeof(int) * (size_t)b.n);
         o_rank[j] = take(sizeof(int) * (size_t)b.n);
         o_tmp[j] = take(sizeof(int) * (size_t)b.n);
-        o_bsum[j] = take(sizeof(int) * (size_t)cdiv(cap_max + 1, kScanChunk));
+        o_bpart[j] = take(sizeof(float) * 5 * (size_t)b.bbox_blocks);
         o_rec[j] = take(sizeof(QRec) * (size_t)std::max<long long>(P->m[j], 1));
         const size_t mq = (size_t)std::max<long long>(P->m[j], 1);
         o_qkey[j] = take(sizeof(int) * mq);
@@ -700,7 +660,9 @@ aidw_status aidw_batch_plan_create(const aidw_job *jobs, int n_jobs, const aidw_
         b.blk_q = blk_q;
         blk_q += cdiv(b.m, kThreads);
         o_start[j] = (size_t)start_ints;  // in ints, inside the start region
-        start_ints += (cap_max + 1 + 63) / 64 * 64;
+        flags_off[j] = (cap_max + 2) / 2 * 2;
+        tick_off[j] = flags_off[j] + 2 * cdiv(cap_max + 1, kScanChunk);
+        start_ints += (tick_off[j] + 4 + 63) / 64 * 64;
 
         WJob &w = P->wj[j];
         memset(&w, 0, sizeof(w));
@@ -718,7 +680,7 @@ aidw_status aidw_batch_plan_create(const aidw_job *jobs, int n_jobs, const aidw_
     }
     P->total_pt_blocks = blk_pt;
     P->total_bbox_blocks = blk_bbox;
-    P->total_pad_blocks = blk_pad;
+    P->total_fp_blocks = blk_fp;
     P->total_q_blocks = blk_q;
     P->total_u = ubase;
     P->total_tiles = tbase;
@@ -769,9 +731,13 @@ aidw_status aidw_batch_plan_create(const aidw_job *jobs, int n_jobs, const aidw_
         b.key = reinterpret_cast<int *>(base + o_key[j]);
         b.rank = reinterpret_cast<int *>(base + o_rank[j]);
         b.tmp = reinterpret_cast<int *>(base + o_tmp[j]);
-        b.bsum = reinterpret_cast<int *>(base + o_bsum[j]);
+        b.bpart = reinterpret_cast<float *>(base + o_bpart[j]);
         b.start = P->start_pool + o_start[j];
+        b.flags = reinterpret_cast<unsigned long long *>(b.start + flags_off[j]);
+        b.tickets = b.start + tick_off[j];
         b.qcount = P->qcount_pool + o_start[j];
+        b.qflags = reinterpret_cast<unsigned long long *>(b.qcount + flags_off[j]);
+        b.qticket = b.qcount + tick_off[j];
         b.qkey = reinterpret_cast<int *>(base + o_qkey[j]);
         b.qrank = reinterpret_cast<int *>(base + o_qrank[j]);
         b.qorder = reinterpret_cast<int *>(base + o_qorder[j]);

@@ -41,7 +41,8 @@ __global__ void __launch_bounds__(kThreads) k_bbox_dims(const float *__restrict_
                                                         GridDev *g, double cell_scale,
                                                         double area_param, long long cap)
 {
-    bbox_dims_block(x, y, z, n, part, ticket, g, cell_scale, area_param, cap);
+    bbox_dims_block(x, y, z, n, part, ticket, g, cell_scale, area_param, cap, blockIdx.x,
+                    gridDim.x);
 }
 
 __global__ void __launch_bounds__(kThreads) k_keys(const float *__restrict__ x,

@@ -16,7 +16,8 @@ constexpr int kThreads = 256;
 constexpr int kScanItems = 16;                     // per thread
 constexpr int kScanChunk = kThreads * kScanItems;  // per block
 
-// Order-preserving integer encoding of float32 for atomicMin/atomicMax.
+// Order-preserving integer encoding of float32 (the form in which the
+// grid record keeps its bounding box).
 __device__ __forceinline__ int enc_float(float f)
 {
     const int b = __float_as_int(f);
@@ -30,88 +31,24 @@ __device__ __forceinline__ float dec_float(int e)
 __device__ __forceinline__ void grid_dims(GridDev *g, double cell_scale, double area_param,
                                           long long cap);
 
-__device__ __forceinline__ void grid_init(GridDev *g, long long n)
-{
-    g->enc_min_x = 0x7FFFFFFF;
-    g->enc_min_y = 0x7FFFFFFF;
-    g->enc_max_x = (int)0x80000000;
-    g->enc_max_y = (int)0x80000000;
-    g->n_data = n;
-    g->status = 0;
-}
-
-// Bounding box of points [first, n) visited with the given stride by this
-// block, merged into g with atomics; also flags non-finite x, y or z.
-// Called by every thread of a block of kThreads threads.
-__device__ __forceinline__ void bbox_block(const float *__restrict__ x, const float *__restrict__ y,
-                                           const float *__restrict__ z, long long first,
-                                           long long n, long long stride, GridDev *g)
-{
-    float mnx = FLT_MAX, mny = FLT_MAX, mxx = -FLT_MAX, mxy = -FLT_MAX;
-    int bad = 0;
-    for (long long i = first; i < n; i += stride) {
-        const float xi = __ldg(x + i), yi = __ldg(y + i), zi = __ldg(z + i);
-        if (!isfinite(xi) || !isfinite(yi) || !isfinite(zi)) {
-            bad = 1;
-            continue;
-        }
-        mnx = fminf(mnx, xi);
-        mxx = fmaxf(mxx, xi);
-        mny = fminf(mny, yi);
-        mxy = fmaxf(mxy, yi);
-    }
-    for (int o = 16; o > 0; o >>= 1) {
-        mnx = fminf(mnx, __shfl_xor_sync(0xffffffffu, mnx, o));
-        mxx = fmaxf(mxx, __shfl_xor_sync(0xffffffffu, mxx, o));
-        mny = fminf(mny, __shfl_xor_sync(0xffffffffu, mny, o));
-        mxy = fmaxf(mxy, __shfl_xor_sync(0xffffffffu, mxy, o));
-    }
-    bad = __any_sync(0xffffffffu, bad);
-    __shared__ float s[4][kThreads / 32];
-    __shared__ int sbad;
-    if (threadIdx.x == 0) sbad = 0;
-    __syncthreads();
-    const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
-    if (l == 0) {
-        s[0][w] = mnx;
-        s[1][w] = mxx;
-        s[2][w] = mny;
-        s[3][w] = mxy;
-        if (bad) sbad = 1;
-    }
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        for (int i = 1; i < kThreads / 32; ++i) {
-            mnx = fminf(mnx, s[0][i]);
-            mxx = fmaxf(mxx, s[1][i]);
-            mny = fminf(mny, s[2][i]);
-            mxy = fmaxf(mxy, s[3][i]);
-        }
-        atomicMin(&g->enc_min_x, enc_float(mnx));
-        atomicMax(&g->enc_max_x, enc_float(mxx));
-        atomicMin(&g->enc_min_y, enc_float(mny));
-        atomicMax(&g->enc_max_y, enc_float(mxy));
-        if (sbad) atomicOr(&g->status, kStatusNonfiniteData);
-    }
-}
-
 // ---- bounding box and dimensions in one launch --------------------------------
-// Each block reduces its points to (min x, max x, min y, max y, non-finite
-// flag) and stores them in part[5 * block]; the last block to finish (an
-// atomic ticket, which it resets for the next launch) reduces the blocks'
-// records, writes the whole grid record (status included, so the record
-// needs no initialisation) and computes the dimensions.
+// The grid's points are reduced by nblocks blocks of kThreads threads; this is
+// block lb of them.  Each block reduces its points to (min x, max x, min y,
+// max y, non-finite flag) and stores them in part[5 * lb]; the last block to
+// finish (an atomic ticket, which it resets for the next launch) reduces the
+// blocks' records, writes the whole grid record (status included, so the
+// record needs no initialisation) and computes the dimensions.
 __device__ __forceinline__ void bbox_dims_block(const float *__restrict__ x,
                                                 const float *__restrict__ y,
                                                 const float *__restrict__ z, long long n,
                                                 float *__restrict__ part, int *ticket, GridDev *g,
                                                 double cell_scale, double area_param,
-                                                long long cap)
+                                                long long cap, long long lb, long long nblocks)
 {
     float mnx = FLT_MAX, mny = FLT_MAX, mxx = -FLT_MAX, mxy = -FLT_MAX;
     int bad = 0;
-    const long long stride = (long long)gridDim.x * blockDim.x;
-    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
+    const long long stride = nblocks * kThreads;
+    for (long long i = lb * kThreads + threadIdx.x; i < n; i += stride) {
         const float xi = __ldg(x + i), yi = __ldg(y + i), zi = __ldg(z + i);
         if (!isfinite(xi) || !isfinite(yi) || !isfinite(zi)) {
             bad = 1;
@@ -152,14 +89,14 @@ __device__ __forceinline__ void bbox_dims_block(const float *__restrict__ x,
         }
         if (round == 1) break;
         if (threadIdx.x == 0) {
-            float *p = part + 5 * (long long)blockIdx.x;
+            float *p = part + 5 * lb;
             p[0] = mnx;
             p[1] = mxx;
             p[2] = mny;
             p[3] = mxy;
             p[4] = bad ? 1.0f : 0.0f;
             __threadfence();
-            last = atomicAdd(ticket, 1) == (int)gridDim.x - 1;
+            last = atomicAdd(ticket, 1) == (int)nblocks - 1;
         }
         __syncthreads();
         if (!last) return;
@@ -169,7 +106,7 @@ __device__ __forceinline__ void bbox_dims_block(const float *__restrict__ x,
         mnx = mny = FLT_MAX;
         mxx = mxy = -FLT_MAX;
         bad = 0;
-        for (int b = threadIdx.x; b < (int)gridDim.x; b += blockDim.x) {
+        for (long long b = threadIdx.x; b < nblocks; b += kThreads) {
             const float *p = part + 5 * (long long)b;
             mnx = fminf(mnx, __ldcg(p + 0));
             mxx = fmaxf(mxx, __ldcg(p + 1));
@@ -323,68 +260,6 @@ __device__ __forceinline__ int block_exclusive_scan(int v, int &total)
     const int r = warp_tot[w] + incl - v;
     __syncthreads();
     return r;
-}
-
-// Sum of chunk `chunk` (kScanChunk elements) of a[0, len) -> *out (block-wide).
-__device__ __forceinline__ void scan_reduce_chunk(const int *__restrict__ a, long long len,
-                                                  long long chunk, int *out)
-{
-    const long long base = chunk * kScanChunk;
-    int s = 0;
-#pragma unroll
-    for (int j = 0; j < kScanItems; ++j) {
-        const long long i = base + (long long)j * kThreads + threadIdx.x;
-        if (i < len) s += a[i];
-    }
-    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
-    __shared__ int ws[kThreads / 32];
-    if ((threadIdx.x & 31) == 0) ws[threadIdx.x >> 5] = s;
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        int t = 0;
-        for (int i = 0; i < kThreads / 32; ++i) t += ws[i];
-        *out = t;
-    }
-}
-
-// Exclusive scan of the nb chunk sums in place (block-wide).
-__device__ __forceinline__ void scan_sums(int *block_sum, int nb)
-{
-    __shared__ int carry;
-    __shared__ int tot;
-    if (threadIdx.x == 0) carry = 0;
-    __syncthreads();
-    for (int base = 0; base < nb; base += kThreads) {
-        const int i = base + threadIdx.x;
-        const int v = i < nb ? block_sum[i] : 0;
-        const int ex = block_exclusive_scan(v, tot);
-        if (i < nb) block_sum[i] = carry + ex;
-        __syncthreads();
-        if (threadIdx.x == 0) carry += tot;
-        __syncthreads();
-    }
-}
-
-// Exclusive scan of chunk `chunk` of a[0, len) in place, starting at offset
-// (block-wide; each thread owns kScanItems consecutive elements).
-__device__ __forceinline__ void scan_apply_chunk(int *__restrict__ a, long long len,
-                                                 long long chunk, int offset)
-{
-    __shared__ int tot;
-    const long long base = chunk * kScanChunk + (long long)threadIdx.x * kScanItems;
-    int v[kScanItems];
-    int s = 0;
-#pragma unroll
-    for (int j = 0; j < kScanItems; ++j) {
-        v[j] = (base + j < len) ? a[base + j] : 0;
-        s += v[j];
-    }
-    int run = offset + block_exclusive_scan(s, tot);
-#pragma unroll
-    for (int j = 0; j < kScanItems; ++j) {
-        if (base + j < len) a[base + j] = run;
-        run += v[j];
-    }
 }
 
 // ---- single-pass exclusive scan (decoupled look-back) --------------------------
