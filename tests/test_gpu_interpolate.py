@@ -85,6 +85,33 @@ def test_hits_duplicates_and_hand_cases(aidw, oracle):
                1e-9 if fp64 else 1e-5)
 
 
+@pytest.mark.parametrize("k", [10, 32])
+def test_more_coincident_points_than_k(aidw, oracle, k):
+    """A query on a location held by more data points than k returns the mean
+    z of all of them (reading Z12, the limit of Eq. 1), not of the k it keeps
+    as neighbours; alpha still comes from the k nearest (all at distance 0
+    there: R = 0, alpha = alpha_1)."""
+    w = inputs.uniform_kilo(n=3000, m=20, seed=11)
+    rng = np.random.default_rng(11)
+    spots = [(123.25, 456.5, 40), (700.0, 10.75, 50), (999.5, 999.5, 33)]
+    xs, ys, zs = [w.x], [w.y], [w.z]
+    for sx, sy, c in spots:
+        xs.append(np.full(c, sx, np.float32))
+        ys.append(np.full(c, sy, np.float32))
+        zs.append(rng.normal(0.0, 10.0, c).astype(np.float32))
+    x, y, z = (np.concatenate(a) for a in (xs, ys, zs))
+    qx = np.concatenate([np.float32([sx for sx, _, _ in spots]), w.qx]).astype(np.float32)
+    qy = np.concatenate([np.float32([sy for _, sy, _ in spots]), w.qy]).astype(np.float32)
+    for fp64 in (False, True):
+        zq, al = _interp(aidw, x, y, z, qx, qy, k, fp64)
+        _check(oracle, x, y, z, qx, qy, k, zq, al, TOL_FP64 if fp64 else TOL_FP32,
+               1e-9 if fp64 else 1e-5)
+        for i in range(len(spots)):
+            mean = zs[1 + i].astype(np.float64).mean()
+            assert abs(float(zq[i]) - mean) <= 1e-6 * max(1.0, abs(mean))
+            assert float(al[i]) == 1.0
+
+
 def test_constant_field_and_affine_map(aidw):
     w = inputs.uniform_kilo(n=20000, m=5000, seed=3)
     zq, _ = _interp(aidw, w.x, w.y, np.full(w.n, 7.5, np.float32), w.qx, w.qy, 10)
