@@ -2,6 +2,7 @@
 #pragma once
 
 #include <cuda_runtime.h>
+#include <nvtx3/nvToolsExt.h>
 #include <stdint.h>
 
 #include "aidw.h"
@@ -76,6 +77,16 @@ struct aidw_grid {
 };
 
 namespace aidw {
+
+// Names the host-side span of a library call or stage for profilers (an
+// NVTX range, e.g. `ncu --nvtx --nvtx-include "aidw_interpolate/"`); a no-op
+// unless such a tool is attached.
+struct NvtxRange {
+    explicit NvtxRange(const char *name) { nvtxRangePushA(name); }
+    ~NvtxRange() { nvtxRangePop(); }
+    NvtxRange(const NvtxRange &) = delete;
+    NvtxRange &operator=(const NvtxRange &) = delete;
+};
 
 // ---- launch helpers (defined in api.cu) -----------------------------------
 aidw_status cuda_status(cudaError_t e);

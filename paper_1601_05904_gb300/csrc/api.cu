@@ -260,6 +260,7 @@ const char *aidw_status_string(aidw_status s)
 aidw_status aidw_grid_build(const float *x, const float *y, const float *z, int64_t n_data,
                             const aidw_params *p, aidw_stream_t stream, aidw_grid **out)
 {
+    NvtxRange nvtx_("aidw_grid_build");
     if (!out) return AIDW_ERR_INVALID_ARG;
     *out = nullptr;
     if (!x || !y || !z || n_data < 1 || n_data > kMaxPoints) return AIDW_ERR_INVALID_ARG;
@@ -393,6 +394,7 @@ aidw_status aidw_knn(const aidw_grid *g, const float *qx, const float *qy, int64
                      int k, int32_t *out_idx, float *out_dist, float *out_robs,
                      aidw_stream_t stream)
 {
+    NvtxRange nvtx_("aidw_knn");
     if (!g || n_query < 0 || n_query > kMaxPoints) return AIDW_ERR_INVALID_ARG;
     if (k < 1 || k > AIDW_MAX_K || k > g->n_data) return AIDW_ERR_K_RANGE;
     if (n_query == 0) return AIDW_OK;
@@ -407,6 +409,7 @@ aidw_status aidw_interpolate(const aidw_grid *g, const float *qx, const float *q
                              int64_t n_query, const aidw_params *p, void *out_z,
                              void *out_alpha, aidw_stream_t stream)
 {
+    NvtxRange nvtx_("aidw_interpolate");
     if (!g || n_query < 0 || n_query > kMaxPoints) return AIDW_ERR_INVALID_ARG;
     const aidw_status ps = check_params(p, true);
     if (ps != AIDW_OK) return ps;
@@ -429,6 +432,7 @@ aidw_status aidw_knn_bruteforce(const aidw_grid *g, const float *qx, const float
                                 int64_t n_query, int k, int32_t *out_idx, float *out_dist,
                                 float *out_robs, aidw_stream_t stream)
 {
+    NvtxRange nvtx_("aidw_knn_bruteforce");
     if (!g || n_query < 0 || n_query > kMaxPoints) return AIDW_ERR_INVALID_ARG;
     if (k < 1 || k > AIDW_MAX_K || k > g->n_data) return AIDW_ERR_K_RANGE;
     if (n_query == 0) return AIDW_OK;
@@ -441,6 +445,7 @@ aidw_status aidw_knn_paper_rule(const aidw_grid *g, const float *qx, const float
                                 int64_t n_query, int k, int32_t *out_idx, float *out_dist,
                                 float *out_robs, aidw_stream_t stream)
 {
+    NvtxRange nvtx_("aidw_knn_paper_rule");
     if (!g || n_query < 0 || n_query > kMaxPoints) return AIDW_ERR_INVALID_ARG;
     if (k < 1 || k > AIDW_MAX_K || k > g->n_data) return AIDW_ERR_K_RANGE;
     if (n_query == 0) return AIDW_OK;
@@ -456,6 +461,7 @@ aidw_status aidw_interpolate_local(const aidw_grid *g, const float *qx, const fl
                                    int64_t n_query, const aidw_params *p, void *out_z,
                                    void *out_alpha, aidw_stream_t stream)
 {
+    NvtxRange nvtx_("aidw_interpolate_local");
     if (!g || n_query < 0 || n_query > kMaxPoints) return AIDW_ERR_INVALID_ARG;
     const aidw_status ps = check_params(p, true);
     if (ps != AIDW_OK) return ps;
@@ -472,6 +478,7 @@ aidw_status aidw_interpolate_host(const float *x, const float *y, const float *z
                                   const aidw_params *p, void *out_z, void *out_alpha,
                                   aidw_stream_t stream)
 {
+    NvtxRange nvtx_("aidw_interpolate_host");
     if (!x || !y || !z || n_data < 1 || n_data > kMaxPoints) return AIDW_ERR_INVALID_ARG;
     if (n_query < 0 || n_query > kMaxPoints) return AIDW_ERR_INVALID_ARG;
     aidw_status st = check_params(p, true);
@@ -532,6 +539,7 @@ aidw_status aidw_interpolate_shard(const aidw_grid *g, const float *qx, const fl
                                    const aidw_params *p, void *out_z, void *out_alpha,
                                    aidw_stream_t stream)
 {
+    NvtxRange nvtx_("aidw_interpolate_shard");
     if (!g || n_query < 0 || n_query > kMaxPoints) return AIDW_ERR_INVALID_ARG;
     int64_t b = 0, e = 0;
     aidw_status st = aidw_shard_range(n_query, shard, n_shards, &b, &e);

@@ -360,6 +360,7 @@ aidw_status enqueue(aidw_batch_plan *P, cudaStream_t s, bool knn_only)
 
 aidw_status capture(aidw_batch_plan *P)
 {
+    NvtxRange nvtx_("graph capture");
     if (P->exec) {
         cudaGraphExecDestroy(P->exec);
         P->exec = nullptr;
@@ -570,6 +571,7 @@ extern "C" {
 aidw_status aidw_batch_plan_create(const aidw_job *jobs, int n_jobs, const aidw_params *p,
                                    aidw_batch_plan **out)
 {
+    NvtxRange nvtx_("aidw_batch_plan_create");
     if (!out) return AIDW_ERR_INVALID_ARG;
     *out = nullptr;
     if (!jobs || n_jobs < 1 || n_jobs > (1 << 20)) return AIDW_ERR_INVALID_ARG;
@@ -804,6 +806,7 @@ aidw_status aidw_batch_plan_create(const aidw_job *jobs, int n_jobs, const aidw_
 
 aidw_status aidw_batch_run(aidw_batch_plan *plan, const aidw_job *jobs, aidw_stream_t stream)
 {
+    NvtxRange nvtx_("aidw_batch_run");
     if (!plan) return AIDW_ERR_INVALID_ARG;
     aidw_status st = check_jobs(plan, jobs, jobs ? plan->n_jobs : 0);
     if (st != AIDW_OK) return st;
@@ -823,6 +826,7 @@ aidw_status aidw_batch_run(aidw_batch_plan *plan, const aidw_job *jobs, aidw_str
 aidw_status aidw_batch_plan_tune(aidw_batch_plan *plan, const aidw_job *jobs,
                                  aidw_stream_t stream, double *best_ms)
 {
+    NvtxRange nvtx_("aidw_batch_plan_tune");
     if (!plan) return AIDW_ERR_INVALID_ARG;
     aidw_status st = check_jobs(plan, jobs, jobs ? plan->n_jobs : 0);
     if (st != AIDW_OK) return st;
@@ -975,6 +979,7 @@ aidw_status aidw_batch_plan_destroy(aidw_batch_plan *plan)
 aidw_status aidw_batch(const aidw_job *jobs, int n_jobs, const aidw_params *p,
                        aidw_stream_t stream)
 {
+    NvtxRange nvtx_("aidw_batch");
     aidw_batch_plan *plan = nullptr;
     aidw_status st = aidw_batch_plan_create(jobs, n_jobs, p, &plan);
     if (st != AIDW_OK) return st;

@@ -119,6 +119,7 @@ long long grid_cell_start_ints(long long cap)
 aidw_status grid_build_launch(aidw_grid *g, const float *x, const float *y, const float *z,
                               cudaStream_t s)
 {
+    NvtxRange nvtx_("grid build");
     const long long n = g->n_data;
     const long long cap = g->cap_cells;
     const long long scan_len = cap + 1;

@@ -893,6 +893,7 @@ aidw_status knn_launch(const aidw_grid *g, const float *qx, const float *qy, lon
                        float *out_dist, float *out_robs, void *out_alpha, cudaStream_t s,
                        void *out_zlocal, bool sort, int stop_rule)
 {
+    NvtxRange nvtx_("knn");
     if (n_query <= 0) return AIDW_OK;
     KnnJob j;
     j.g = g->dev;

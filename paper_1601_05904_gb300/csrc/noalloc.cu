@@ -55,6 +55,7 @@ extern "C" aidw_status aidw_interpolate_noalloc(const aidw_grid *g, const float 
                                                 void *out_alpha, aidw_stream_t stream)
 {
     using namespace aidw;
+    NvtxRange nvtx_("aidw_interpolate_noalloc");
     if (!g || n_query < 0 || n_query > AIDW_NOALLOC_MAX_QUERIES) return AIDW_ERR_INVALID_ARG;
     const aidw_status ps = api_detail::check_params(p, true);
     if (ps != AIDW_OK) return ps;

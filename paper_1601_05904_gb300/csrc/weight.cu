@@ -615,6 +615,7 @@ int g_hook_tries = 0;
 template <bool F64>
 aidw_status launch(SKArgs a, void *part, cudaStream_t s)
 {
+    NvtxRange nvtx_("weighting");
     a.wait_tries = kWaitTries;
     a.skip_unit = -1;
     cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;

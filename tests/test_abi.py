@@ -158,3 +158,44 @@ def test_host_entry_point_checks_arguments_without_a_gpu(lib):
     p5 = _params(k=5)
     assert f(a, a, a, 4, a, a, 4, ctypes.byref(p5), out, None, None) == 2   # k > n_data
     del binding
+
+
+def _nvtx_recorder(tmp_path):
+    """Builds the test NVTX tool (tests/c_abi/nvtx_recorder.c)."""
+    cuda_inc = "/usr/local/cuda/include"
+    nvcc = shutil.which("nvcc")
+    if nvcc:
+        cuda_inc = os.path.join(os.path.dirname(os.path.dirname(os.path.realpath(nvcc))), "include")
+    out = str(tmp_path / "nvtx_recorder.so")
+    import subprocess
+    r = subprocess.run(["gcc", "-O2", "-std=c11", "-shared", "-fPIC", "-I", cuda_inc,
+                        os.path.join(ROOT, "tests", "c_abi", "nvtx_recorder.c"), "-o", out],
+                       capture_output=True, text=True)
+    assert r.returncode == 0, r.stderr
+    return out
+
+
+def test_entry_points_open_and_close_named_nvtx_ranges(lib, tmp_path):
+    """Every C-ABI call opens an NVTX range named after it and closes it on
+    every return path, the argument errors included (no GPU needed)."""
+    import subprocess
+    import sys
+    rec = _nvtx_recorder(tmp_path)
+    log = tmp_path / "nvtx.log"
+    script = (
+        "import ctypes\n"
+        "from paper_1601_05904_gb300 import binding\n"
+        "lib = binding.load()\n"
+        "pc = binding.Params(k=2).to_c()\n"
+        "a = (ctypes.c_float * 4)(); out = (ctypes.c_float * 4)()\n"
+        "assert lib.aidw_interpolate_host(None, a, a, 4, a, a, 4, ctypes.byref(pc), out, None, None) == 1\n"
+        "assert lib.aidw_interpolate_shard(None, None, None, 4, 0, 1, ctypes.byref(pc), None, None, None) == 1\n"
+        "assert lib.aidw_batch_run(None, None, None) == 1\n")
+    env = dict(os.environ, NVTX_INJECTION64_PATH=rec, AIDW_NVTX_LOG=str(log),
+               PYTHONPATH=ROOT)
+    r = subprocess.run([sys.executable, "-c", script], env=env, capture_output=True, text=True,
+                       timeout=120)
+    assert r.returncode == 0, r.stderr
+    assert log.read_text().split("\n")[:-1] == [
+        "push aidw_interpolate_host", "pop", "push aidw_interpolate_shard", "pop",
+        "push aidw_batch_run", "pop"]

@@ -68,3 +68,60 @@ def test_c_client_matches_the_oracle(client, oracle, tmp_path):
                                    loc["scale"]).max() <= TOL_FP32
     check_knn(oracle, w.x, w.y, w.qx, w.qy, w.k, load("idx.bin", np.int32, (w.m, w.k)),
               load("dist.bin", np.float32, (w.m, w.k)), load("robs.bin", np.float32))
+
+
+def _nvtx_tree(lines):
+    """Parses the recorder's "push name" / "pop" lines into (name, children)."""
+    root = ("", [])
+    stack = [root]
+    for ln in lines:
+        if ln.startswith("push "):
+            node = (ln[5:], [])
+            stack[-1][1].append(node)
+            stack.append(node)
+        else:
+            assert ln == "pop" and len(stack) > 1, "pop without push"
+            stack.pop()
+    assert len(stack) == 1, "ranges left open"
+    return root[1]
+
+
+def test_nvtx_ranges_name_each_call_and_its_stages(aidw, tmp_path):
+    """With an NVTX tool attached, the grid build, the interpolation and the
+    batch each appear as a range named after the C-ABI call, with the stages
+    they launch (grid build; kNN, weighting; graph capture) nested inside."""
+    import sys
+    from paper_1601_05904_gb300 import build
+    build.build()
+    rec = str(tmp_path / "nvtx_recorder.so")
+    r = subprocess.run(["gcc", "-O2", "-std=c11", "-shared", "-fPIC",
+                        "-I", os.path.join(_cuda_home(), "include"),
+                        os.path.join(HERE, "c_abi", "nvtx_recorder.c"), "-o", rec],
+                       capture_output=True, text=True)
+    assert r.returncode == 0, r.stderr
+    log = tmp_path / "nvtx.log"
+    script = (
+        "import numpy as np, torch\n"
+        "from paper_1601_05904_gb300 import binding as b, inputs\n"
+        "w = inputs.uniform_kilo(n=5000, m=700, seed=62)\n"
+        "d = lambda a: torch.from_numpy(np.ascontiguousarray(a)).cuda()\n"
+        "p = b.Params(k=10)\n"
+        "g = b.aidw_grid_build(d(w.x), d(w.y), d(w.z), p)\n"
+        "z, _ = b.aidw_interpolate(g, d(w.qx), d(w.qy), p)\n"
+        "jobs = [b.BatchJob(d(w.x), d(w.y), d(w.z), d(w.qx), d(w.qy), k) for k in (6, 10)]\n"
+        "b.aidw_batch(jobs, p)\n"
+        "torch.cuda.synchronize()\n"
+        "assert bool(torch.isfinite(z).all())\n")
+    env = dict(os.environ, NVTX_INJECTION64_PATH=rec, AIDW_NVTX_LOG=str(log), PYTHONPATH=ROOT)
+    r = subprocess.run([sys.executable, "-c", script], env=env, capture_output=True, text=True,
+                       timeout=300)
+    assert r.returncode == 0, r.stderr
+    tree = _nvtx_tree(log.read_text().split("\n")[:-1])
+    top = [n for n, _ in tree]
+    assert top == ["aidw_grid_build", "aidw_interpolate", "aidw_batch"], top
+    kids = {n: [c for c, _ in ch] for n, ch in tree}
+    assert kids["aidw_grid_build"] == ["grid build"]
+    assert kids["aidw_interpolate"] == ["knn", "weighting"]
+    assert kids["aidw_batch"] == ["aidw_batch_plan_create", "aidw_batch_run"]
+    run = dict(tree)["aidw_batch"][1][1]
+    assert [c for c, _ in run] == ["graph capture"]
