@@ -151,7 +151,9 @@ struct WJob {
     const QRec *recs;
     void *out_z;
     long long n_data, n_pad;
-    long long D, T;    // data tiles, query tiles
+    long long D, T;    // data units (pieces of weighting tiles), query tiles
+    int piece_shift;   // a data unit is 1/2^piece_shift of a weighting tile
+                       // (float32 path; 0 on the float64 path)
     long long nq;
     long long unit_base, tile_base, q_base;
 };

@@ -1,11 +1,12 @@
 // Weighting stage: Eq. 1 of arXiv 1601.05904 summed over ALL data points.
 //
 // Work decomposition (stream-K).  The pair space is cut into units of one
-// query tile (kQPT queries per thread x kThreads threads) by one data tile
-// (kDTile cell-ordered points).  Units are numbered tile-major
-// (u = t * D + d) and every resident CTA of a persistent grid takes one
-// contiguous, equal share of them, so all SMs finish together whatever the
-// query count.  A CTA's share covers the tail of one query tile, whole tiles
+// query tile (kQPT queries per thread x kThreads threads) by one piece of a
+// data tile (kDTile cell-ordered points, or 1/2 .. 1/16 of them when the
+// point set is too small to give every CTA several whole tiles).  Units are
+// numbered tile-major (u = t * D + d) and every resident CTA of a persistent
+// grid takes one contiguous, equal share of them, so all SMs finish together
+// whatever the query count.  A CTA's share covers the tail of one query tile, whole tiles
 // and the head of another; for each query tile it touches it writes one
 // partial (sum w, sum w z) per query to slot (tile + cta) of a scratch array,
 // and a finalize kernel adds the pieces of each query in CTA order
@@ -164,13 +165,17 @@ __device__ __forceinline__ WJob job_of_query(const SKArgs &a, long long gq)
     return a.jobs[lo];
 }
 
-// Points of data tile d that the float32 kernel processes: the valid ones
-// rounded up to kChunk2 (the tile's padding has weight 0).
-__device__ __forceinline__ int soa_count(long long n_data, long long d)
+// Points of data unit d (pieces of kDTile >> shift points) that the float32
+// kernel processes: the valid ones rounded up to kChunk2 (the tile's padding
+// has weight 0).
+constexpr int kMaxPieceShift = 4;
+static_assert((kDTile >> kMaxPieceShift) % kChunk2 == 0, "pieces are whole chunks");
+__host__ __device__ __forceinline__ int soa_count(long long n_data, long long d, int shift)
 {
-    const long long rem = n_data - d * kDTile;
+    const long long piece = kDTile >> shift;
+    const long long rem = n_data - d * piece;
     const long long c = (rem + kChunk2 - 1) / kChunk2 * kChunk2;
-    return (int)min((long long)kDTile, c);
+    return (int)(c < piece ? c : piece);
 }
 
 // Points of data tile d in the float64 kernel's AoS layout.
@@ -186,8 +191,12 @@ __device__ __forceinline__ void issue_tile_soa(const SKArgs &a, float *buf, uint
     if (HOOK && u == a.skip_unit) return;
     const WJob J = job_of_unit(a, u);
     const long long d = (u - J.unit_base) % J.D;
-    const uint32_t bytes = (uint32_t)soa_count(J.n_data, d) * 4u;
-    const float *src = J.wt + d * (3 * kDTile);
+    const uint32_t bytes = (uint32_t)soa_count(J.n_data, d, J.piece_shift) * 4u;
+    // piece d is piece (d mod 2^shift) of weighting tile (d >> shift); pieces
+    // are multiples of kChunk2 points, so every copy starts 512-byte aligned
+    const long long piece = kDTile >> J.piece_shift;
+    const float *src = J.wt + (d >> J.piece_shift) * (3 * kDTile) +
+                       (d & ((1LL << J.piece_shift) - 1)) * piece;
     mbar_expect_tx(bar, 3u * bytes);
     bulk_g2s(buf, src, bytes, bar);
     bulk_g2s(buf + kDTile, src + kDTile, bytes, bar);
@@ -280,7 +289,7 @@ __global__ void __launch_bounds__(THREADS, MINB)
             const float *X = buf + s * 3 * kDTile;
             const float *Y = X + kDTile;
             const float *Z = Y + kDTile;
-            const int cnt = soa_count(J.n_data, (u - J.unit_base) % J.D);
+            const int cnt = soa_count(J.n_data, (u - J.unit_base) % J.D, J.piece_shift);
             if (ok) {
                 for (int c0 = 0; c0 < cnt; c0 += kChunk2) {
                     F2 ps[Q], pz[Q];
@@ -656,10 +665,43 @@ aidw_status launch(SKArgs a, void *part, cudaStream_t s)
     return cuda_status(cudaGetLastError());
 }
 
-// The single job of a grid and one query set.
+// Pieces per weighting tile (as a shift) for one job of n_data points and T
+// query tiles on at most G_max CTAs: the shift whose largest CTA share, in
+// points, is smallest, each unit charged kUnitCost points more for its
+// barrier wait, copy issue and chunk folds.  Whole tiles unless the point
+// set is too small to give every CTA several of them (at n = m = 10,240:
+// 50 whole-tile units for 304 CTAs, against 800 units of 128 points).
+// AIDW_WEIGHT_PIECES=s (0..4) fixes the shift, for measurement.
+int piece_shift_for(long long n_data, long long T, long long G_max)
+{
+    static const int forced = [] {
+        const char *e = getenv("AIDW_WEIGHT_PIECES");
+        int v = -1;
+        if (e && sscanf(e, "%d", &v) == 1 && v >= 0 && v <= kMaxPieceShift) return v;
+        return -1;
+    }();
+    if (forced >= 0) return forced;
+    constexpr double kUnitCost = 16.0;
+    int best = 0;
+    double best_cost = 0.0;
+    for (int sh = 0; sh <= kMaxPieceShift; ++sh) {
+        const long long piece = kDTile >> sh;
+        const long long U = T * ((n_data + piece - 1) / piece);
+        const long long G = std::max(1LL, std::min(G_max, U));
+        const double cost =
+            (double)((U + G - 1) / G) * ((double)soa_count(n_data, 0, sh) + kUnitCost);
+        if (sh == 0 || cost < best_cost) {
+            best = sh;
+            best_cost = cost;
+        }
+    }
+    return best;
+}
+
+// The single job of a grid and one query set, on at most G_max CTAs.
 template <bool F64>
 SKArgs single_job(const aidw_grid *g, const float *qx, const float *qy, long long nq,
-                  const QRec *recs, void *out_z)
+                  const QRec *recs, void *out_z, long long G_max)
 {
     using C = WCfg<F64>;
     SKArgs a;
@@ -673,12 +715,15 @@ SKArgs single_job(const aidw_grid *g, const float *qx, const float *qy, long lon
     J.out_z = out_z;
     J.n_data = g->n_data;
     J.n_pad = g->n_pad;
-    J.D = weight_data_tiles(g->n_data, g->n_pad, F64);
     J.T = (nq + C::kQTile - 1) / C::kQTile;
+    J.piece_shift = F64 ? 0 : piece_shift_for(g->n_data, J.T, G_max);
+    const long long piece = kDTile >> J.piece_shift;
+    J.D = F64 ? weight_data_tiles(g->n_data, g->n_pad, true) : (g->n_data + piece - 1) / piece;
     J.nq = nq;
     a.jobs = nullptr;
     a.n_jobs = 1;
     a.U = J.T * J.D;
+    a.G = std::max(1LL, std::min(G_max, a.U));
     a.total_q = nq;
     a.status = &g->dev->status;
     return a;
@@ -689,8 +734,7 @@ aidw_status run(const aidw_grid *g, const float *qx, const float *qy, long long 
                 const QRec *recs, void *out_z, cudaStream_t s)
 {
     using C = WCfg<F64>;
-    SKArgs a = single_job<F64>(g, qx, qy, nq, recs, out_z);
-    a.G = std::min<long long>(resident_ctas<F64>(g->device), a.U);
+    SKArgs a = single_job<F64>(g, qx, qy, nq, recs, out_z, resident_ctas<F64>(g->device));
     void *part = nullptr;
     const size_t part_bytes = sizeof(typename C::Part) * (size_t)C::kQTile * (size_t)(a.job0.T + a.G);
     if (lib_alloc(&part, part_bytes + 256, s) != cudaSuccess) return AIDW_ERR_OOM;
@@ -706,13 +750,14 @@ aidw_status run_scratch(const aidw_grid *g, const float *qx, const float *qy, lo
                         cudaStream_t s)
 {
     using C = WCfg<F64>;
-    SKArgs a = single_job<F64>(g, qx, qy, nq, recs, out_z);
     const long long slot_bytes = (long long)sizeof(typename C::Part) * C::kQTile;
     if (scratch_bytes < 512) return AIDW_ERR_INVALID_ARG;
     const size_t part_room = scratch_bytes - 256;  // the last 256 bytes hold the flag
-    const long long g_fit = (long long)(part_room / (size_t)slot_bytes) - a.job0.T;
+    const long long T = (nq + C::kQTile - 1) / C::kQTile;
+    const long long g_fit = (long long)(part_room / (size_t)slot_bytes) - T;
     if (g_fit < 1) return AIDW_ERR_INVALID_ARG;
-    a.G = std::min<long long>(std::min<long long>(resident_ctas<F64>(g->device), a.U), g_fit);
+    SKArgs a = single_job<F64>(g, qx, qy, nq, recs, out_z,
+                               std::min<long long>(resident_ctas<F64>(g->device), g_fit));
     a.fail = reinterpret_cast<int *>(static_cast<unsigned char *>(scratch) + part_room);
     return launch<F64>(a, scratch, s);
 }
