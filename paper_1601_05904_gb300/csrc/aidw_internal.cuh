@@ -59,6 +59,7 @@ struct QRec {
 
 // Host-side grid handle (the opaque aidw_grid of the C ABI).
 struct aidw_grid {
+    void *block;                 // the one pool allocation holding the buffers below
     aidw::GridDev *dev;          // device struct
     aidw::Point *pts;            // [n_pad] cell-ordered points, padded
     int *cell_start;             // [cap + 1] head of each cell (int32), then the

@@ -282,28 +282,44 @@ aidw_status aidw_grid_build(const float *x, const float *y, const float *z, int6
     g->area_param = p->area > 0.0 ? p->area : 0.0;
     g->cap_cells = grid_cells_capacity(n_data, g->cell_scale);
 
-    cudaError_t e = lib_alloc((void **)&g->dev, sizeof(GridDev), s);
-    if (e == cudaSuccess) e = lib_alloc((void **)&g->pts, sizeof(Point) * (size_t)g->n_pad, s);
-    if (e == cudaSuccess)
-        e = lib_alloc((void **)&g->cell_start, sizeof(int) * (size_t)grid_cell_start_ints(g->cap_cells),
-                      s);
-    if (e == cudaSuccess) e = lib_alloc((void **)&g->perm, sizeof(int) * (size_t)n_data, s);
+    // every buffer of the grid in one pool allocation (256-byte aligned parts)
     g->n_wtiles = (n_data + kWeightTile - 1) / kWeightTile;
-    if (e == cudaSuccess)
-        e = lib_alloc((void **)&g->wt, sizeof(float) * 3 * kWeightTile * (size_t)g->n_wtiles, s);
-    if (e == cudaSuccess) e = lib_alloc((void **)&g->zorig, sizeof(float) * (size_t)n_data, s);
-    if (e == cudaSuccess)
+    size_t off = 0;
+    const auto part = [&off](size_t bytes) {
+        const size_t at = off;
+        off += (bytes + 255) / 256 * 256;
+        return at;
+    };
+    const size_t o_dev = part(sizeof(GridDev));
+    const size_t o_pts = part(sizeof(Point) * (size_t)g->n_pad);
+    const size_t o_start = part(sizeof(int) * (size_t)grid_cell_start_ints(g->cap_cells));
+    const size_t o_perm = part(sizeof(int) * (size_t)n_data);
+    const size_t o_wt = part(sizeof(float) * 3 * kWeightTile * (size_t)g->n_wtiles);
+    const size_t o_zorig = part(sizeof(float) * (size_t)n_data);
+    cudaError_t e = lib_alloc(&g->block, off, s);
+    if (e == cudaSuccess) {
+        unsigned char *base = static_cast<unsigned char *>(g->block);
+        g->dev = reinterpret_cast<GridDev *>(base + o_dev);
+        g->pts = reinterpret_cast<Point *>(base + o_pts);
+        g->cell_start = reinterpret_cast<int *>(base + o_start);
+        g->perm = reinterpret_cast<int *>(base + o_perm);
+        g->wt = reinterpret_cast<float *>(base + o_wt);
+        g->zorig = reinterpret_cast<float *>(base + o_zorig);
         e = cudaMemcpyAsync(g->zorig, z, sizeof(float) * (size_t)n_data, cudaMemcpyDeviceToDevice, s);
+    }
     if (e != cudaSuccess) {
         cudaGetLastError();
         aidw_grid_destroy(g);
         return e == cudaErrorMemoryAllocation ? AIDW_ERR_OOM : AIDW_ERR_CUDA;
     }
     aidw_status st = grid_build_launch(g, x, y, z, s);
-    if (st == AIDW_OK) st = cuda_status(cudaStreamSynchronize(s));
     if (st == AIDW_OK) {
-        st = cuda_status(cudaMemcpy(&g->host_copy, g->dev, sizeof(GridDev),
-                                    cudaMemcpyDeviceToHost));
+        // one stream-ordered read of the device record (dimensions, status)
+        st = cuda_status(cudaMemcpyAsync(&g->host_copy, g->dev, sizeof(GridDev),
+                                         cudaMemcpyDeviceToHost, s));
+        if (st == AIDW_OK) st = cuda_status(cudaStreamSynchronize(s));
+    }
+    if (st == AIDW_OK) {
         const int status = g->host_copy.status;
         if (st == AIDW_OK && (status & kStatusNonfiniteData)) st = AIDW_ERR_NONFINITE;
         if (st == AIDW_OK && (status & kStatusCapacity)) st = AIDW_ERR_INVALID_ARG;
@@ -338,16 +354,20 @@ aidw_status aidw_grid_destroy(aidw_grid *g)
     if (!g) return AIDW_ERR_INVALID_ARG;
     aidw_status st = AIDW_OK;
     if (g->dev) {
-        // drain all work that may still read the grid
-        st = aidw_grid_status(g);
+        // drain all work that may still read the grid, then report its status
+        // as aidw_grid_status would (the record dies with the grid: no reset)
+        cudaError_t e = cudaDeviceSynchronize();
+        int status = 0;
+        if (e == cudaSuccess)
+            e = cudaMemcpy(&status, &g->dev->status, sizeof(int), cudaMemcpyDeviceToHost);
+        st = e != cudaSuccess                                          ? cuda_status(e)
+             : (status & kStatusTimeout)                               ? AIDW_ERR_TIMEOUT
+             : (status & (kStatusNonfiniteData | kStatusNonfiniteQuery)) ? AIDW_ERR_NONFINITE
+             : (status & kStatusCapacity)                              ? AIDW_ERR_INVALID_ARG
+                                                                       : AIDW_OK;
     }
     // the device is idle (drained above); return the buffers to the pool
-    lib_free(g->zorig, nullptr);
-    lib_free(g->wt, nullptr);
-    lib_free(g->perm, nullptr);
-    lib_free(g->cell_start, nullptr);
-    lib_free(g->pts, nullptr);
-    lib_free(g->dev, nullptr);
+    lib_free(g->block, nullptr);
     delete g;
     return st;
 }
