@@ -47,7 +47,8 @@ struct BJob {
     int *start;
     int *perm;
     float *wt;
-    int *key, *rank, *tmp;
+    int *key, *rank;
+    Point *tmp;  // points in cell order, unstable within a cell
     float *bpart;                      // bounding-box records, 5 per block
     // zeroed at the start of every run, after the cell heads in the start
     // region: the scan's chunk records and the tickets (bounding box, scan)
@@ -112,7 +113,7 @@ __global__ void __launch_bounds__(kThreads) k_b_scatter(const BJob *__restrict__
     const BJob &J = jobs[job_of_block<&BJob::blk_pt>(jobs, n_jobs, blockIdx.x)];
     const long long i = (blockIdx.x - J.blk_pt) * kThreads + threadIdx.x;
     if (i >= J.n || grid_failed(J.g)) return;
-    scatter_one(i, J.start, J.key, J.rank, J.tmp);
+    scatter_point(i, J.x, J.y, J.z, J.start, J.key, J.rank, J.tmp);
 }
 
 __global__ void __launch_bounds__(kThreads) k_b_fixup_pad(const BJob *__restrict__ jobs,
@@ -121,7 +122,7 @@ __global__ void __launch_bounds__(kThreads) k_b_fixup_pad(const BJob *__restrict
     const BJob &J = jobs[job_of_block<&BJob::blk_fp>(jobs, n_jobs, blockIdx.x)];
     const long long s = (blockIdx.x - J.blk_fp) * kThreads + threadIdx.x;
     if (s < J.n) {
-        if (!grid_failed(J.g)) fixup_one(s, J.x, J.y, J.z, J.start, J.key, J.tmp, J.pts, J.perm, J.wt);
+        if (!grid_failed(J.g)) fixup_one(s, J.g, J.start, J.tmp, J.pts, J.perm, J.wt);
     } else if (s < (J.n_pad > J.n_wpad ? J.n_pad : J.n_wpad)) {
         pad_one(s, J.n_pad, J.n_wpad, J.pts, J.wt);
     }
@@ -651,7 +652,7 @@ aidw_status aidw_batch_plan_create(const aidw_job *jobs, int n_jobs, const aidw_
         o_perm[j] = take(sizeof(int) * (size_t)b.n);
         o_key[j] = take(sizeof(int) * (size_t)b.n);
         o_rank[j] = take(sizeof(int) * (size_t)b.n);
-        o_tmp[j] = take(sizeof(int) * (size_t)b.n);
+        o_tmp[j] = take(sizeof(Point) * (size_t)b.n);
         o_bpart[j] = take(sizeof(float) * 5 * (size_t)b.bbox_blocks);
         o_rec[j] = take(sizeof(QRec) * (size_t)std::max<long long>(P->m[j], 1));
         const size_t mq = (size_t)std::max<long long>(P->m[j], 1);
@@ -732,7 +733,7 @@ aidw_status aidw_batch_plan_create(const aidw_job *jobs, int n_jobs, const aidw_
         b.perm = reinterpret_cast<int *>(base + o_perm[j]);
         b.key = reinterpret_cast<int *>(base + o_key[j]);
         b.rank = reinterpret_cast<int *>(base + o_rank[j]);
-        b.tmp = reinterpret_cast<int *>(base + o_tmp[j]);
+        b.tmp = reinterpret_cast<Point *>(base + o_tmp[j]);
         b.bpart = reinterpret_cast<float *>(base + o_bpart[j]);
         b.start = P->start_pool + o_start[j];
         b.flags = reinterpret_cast<unsigned long long *>(b.start + flags_off[j]);

@@ -63,33 +63,32 @@ __global__ void __launch_bounds__(kThreads) k_scan(int *__restrict__ a, long lon
     scan_lookback_block(a, len, flags, ticket, &g->status);
 }
 
-__global__ void __launch_bounds__(kThreads) k_scatter(long long n, const GridDev *__restrict__ g,
+__global__ void __launch_bounds__(kThreads) k_scatter(const float *__restrict__ x,
+                                                      const float *__restrict__ y,
+                                                      const float *__restrict__ z, long long n,
+                                                      const GridDev *__restrict__ g,
                                                       const int *__restrict__ start,
                                                       const int *__restrict__ key,
                                                       const int *__restrict__ rank,
-                                                      int *__restrict__ tmp)
+                                                      Point *__restrict__ tmp)
 {
     const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n || grid_failed(g)) return;
-    scatter_one(i, start, key, rank, tmp);
+    scatter_point(i, x, y, z, start, key, rank, tmp);
 }
 
-__global__ void __launch_bounds__(kThreads) k_fixup_pad(const float *__restrict__ x,
-                                                        const float *__restrict__ y,
-                                                        const float *__restrict__ z, long long n,
-                                                        long long pad_hi, long long n_pad,
-                                                        long long n_wpad,
+__global__ void __launch_bounds__(kThreads) k_fixup_pad(long long n, long long pad_hi,
+                                                        long long n_pad, long long n_wpad,
                                                         const GridDev *__restrict__ g,
                                                         const int *__restrict__ start,
-                                                        const int *__restrict__ key,
-                                                        const int *__restrict__ tmp,
+                                                        const Point *__restrict__ tmp,
                                                         Point *__restrict__ pts,
                                                         int *__restrict__ perm,
                                                         float *__restrict__ wt)
 {
     const long long s = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (s < n) {
-        if (!grid_failed(g)) fixup_one(s, x, y, z, start, key, tmp, pts, perm, wt);
+        if (!grid_failed(g)) fixup_one(s, g, start, tmp, pts, perm, wt);
     } else if (s < pad_hi) {
         pad_one(s, n_pad, n_wpad, pts, wt);
     }
@@ -128,11 +127,12 @@ aidw_status grid_build_launch(aidw_grid *g, const float *x, const float *y, cons
     cudaDeviceGetAttribute(&dev_sms, cudaDevAttrMultiProcessorCount, g->device);
     const unsigned bb = (unsigned)std::min<long long>(blocks_for(n, kThreads),
                                                       (long long)dev_sms * 4);
-    int *key = nullptr, *rank = nullptr, *tmp = nullptr;
+    int *key = nullptr, *rank = nullptr;
+    Point *tmp = nullptr;
     float *bpart = nullptr;
     cudaError_t e = lib_alloc((void **)&key, sizeof(int) * n, s);
     if (e == cudaSuccess) e = lib_alloc((void **)&rank, sizeof(int) * n, s);
-    if (e == cudaSuccess) e = lib_alloc((void **)&tmp, sizeof(int) * n, s);
+    if (e == cudaSuccess) e = lib_alloc((void **)&tmp, sizeof(Point) * n, s);
     if (e == cudaSuccess) e = lib_alloc((void **)&bpart, sizeof(float) * 5 * bb, s);
     if (e != cudaSuccess) {
         lib_free(key, s);
@@ -153,11 +153,12 @@ aidw_status grid_build_launch(aidw_grid *g, const float *x, const float *y, cons
                                         g->area_param, cap);
     k_keys<<<blocks_for(n, kThreads), kThreads, 0, s>>>(x, y, n, g->dev, start, key, rank);
     k_scan<<<(unsigned)nb, kThreads, 0, s>>>(start, scan_len, flags, tickets + 1, g->dev);
-    k_scatter<<<blocks_for(n, kThreads), kThreads, 0, s>>>(n, g->dev, start, key, rank, tmp);
+    k_scatter<<<blocks_for(n, kThreads), kThreads, 0, s>>>(x, y, z, n, g->dev, start, key, rank,
+                                                           tmp);
     const long long n_wpad = g->n_wtiles * kWeightTile;
     const long long pad_hi = std::max(std::max(g->n_pad, n_wpad), n);
     k_fixup_pad<<<blocks_for(pad_hi, kThreads), kThreads, 0, s>>>(
-        x, y, z, n, pad_hi, g->n_pad, n_wpad, g->dev, start, key, tmp, g->pts, g->perm, g->wt);
+        n, pad_hi, g->n_pad, n_wpad, g->dev, start, tmp, g->pts, g->perm, g->wt);
     nl += 5;
     lib_free(key, s);
     lib_free(rank, s);

@@ -209,18 +209,24 @@ __device__ __forceinline__ long long cell_floor(float x, float min_f, float inv_
     return (long long)floor(((double)x - min_d) / cw);
 }
 
-// Cell of the point (x, y) stored as item i, and its (unstable) rank among
-// the items of that cell.
-__device__ __forceinline__ void key_one_xy(long long i, float x, float y, const GridDev *g,
-                                           int *__restrict__ count, int *__restrict__ key,
-                                           int *__restrict__ rank)
+// Row-major cell of the point (x, y), clamped to the grid.
+__device__ __forceinline__ int cell_index(float x, float y, const GridDev *g)
 {
     const long long nc = g->n_col, nr = g->n_row;
     long long col = cell_floor(x, g->min_x_f, g->inv_cw_f, g->min_x, g->cw);
     long long row = cell_floor(y, g->min_y_f, g->inv_cw_f, g->min_y, g->cw);
     col = col < 0 ? 0 : (col > nc - 1 ? nc - 1 : col);
     row = row < 0 ? 0 : (row > nr - 1 ? nr - 1 : row);
-    const int c = (int)(row * nc + col);
+    return (int)(row * nc + col);
+}
+
+// Cell of the point (x, y) stored as item i, and its (unstable) rank among
+// the items of that cell.
+__device__ __forceinline__ void key_one_xy(long long i, float x, float y, const GridDev *g,
+                                           int *__restrict__ count, int *__restrict__ key,
+                                           int *__restrict__ rank)
+{
+    const int c = cell_index(x, y, g);
     key[i] = c;
     rank[i] = atomicAdd(count + c, 1);
 }
@@ -360,27 +366,41 @@ __device__ __forceinline__ void scatter_one(long long i, const int *__restrict__
     tmp[start[key[i]] + rank[i]] = (int)i;
 }
 
-// Position s holds some point i of cell c = key[i]; its stable place is the
-// head of c plus the number of indices smaller than i in c's segment.  The
-// point is written there in both layouts.
-__device__ __forceinline__ void fixup_one(long long s, const float *__restrict__ x,
-                                          const float *__restrict__ y,
-                                          const float *__restrict__ z,
-                                          const int *__restrict__ start,
-                                          const int *__restrict__ key,
-                                          const int *__restrict__ tmp, Point *__restrict__ pts,
-                                          int *__restrict__ perm, float *__restrict__ wt)
+// Data point i goes to its cell's segment (in arrival order) as a whole
+// record, read here in input order: the fix-up then reads the records back
+// in cell order instead of gathering x, y, z and the key of each point from
+// arrays that, past a few million points, no longer fit in L2.
+__device__ __forceinline__ void scatter_point(long long i, const float *__restrict__ x,
+                                              const float *__restrict__ y,
+                                              const float *__restrict__ z,
+                                              const int *__restrict__ start,
+                                              const int *__restrict__ key,
+                                              const int *__restrict__ rank,
+                                              Point *__restrict__ tmp)
 {
-    const int i = tmp[s];
-    const int c = key[i];
-    const int a = start[c], b = start[c + 1];
-    int r = 0;
-    for (int t = a; t < b; ++t) r += (tmp[t] < i);
     Point p;
     p.x = x[i];
     p.y = y[i];
     p.z = z[i];
-    p.idx = i;
+    p.idx = (int)i;
+    tmp[start[key[i]] + rank[i]] = p;
+}
+
+// Position s holds some point i of cell c (recomputed from its coordinates
+// by the arithmetic that keyed it); its stable place is the head of c plus
+// the number of indices smaller than i in c's segment.  The point is
+// written there in both layouts.
+__device__ __forceinline__ void fixup_one(long long s, const GridDev *__restrict__ g,
+                                          const int *__restrict__ start,
+                                          const Point *__restrict__ tmp, Point *__restrict__ pts,
+                                          int *__restrict__ perm, float *__restrict__ wt)
+{
+    const Point p = tmp[s];
+    const int i = p.idx;
+    const int c = cell_index(p.x, p.y, g);
+    const int a = start[c], b = start[c + 1];
+    int r = 0;
+    for (int t = a; t < b; ++t) r += (tmp[t].idx < i);
     const long long pos = (long long)a + r;
     pts[pos] = p;
     perm[pos] = i;
