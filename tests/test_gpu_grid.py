@@ -46,6 +46,18 @@ def test_grid_clustered(aidw, oracle):
     _compare(aidw, oracle, w.x, w.y, 2.0)
 
 
+def test_grid_beyond_l2_size(aidw, oracle):
+    """Point sets whose sort arrays (16-byte records, cell heads, keys) are
+    larger than the 129 MB L2, where the scatter and the fix-up work out of
+    DRAM: 8M uniform points (about one per cell) and 4M clustered points
+    (long cell segments for the stable fix-up)."""
+    rng = np.random.default_rng(8)
+    x, y = inputs.uniform_points(rng, 1 << 23, 0.0, 1000.0)
+    _compare(aidw, oracle, x, y, 2.0)
+    w = inputs.clustered_kilo(n=1 << 22, m=1, seed=9)
+    _compare(aidw, oracle, w.x, w.y, 1.0)
+
+
 def test_grid_duplicates_and_cell_boundaries(aidw, oracle):
     # integer lattice with repeats: many points exactly on cell edges
     rng = np.random.default_rng(4)
