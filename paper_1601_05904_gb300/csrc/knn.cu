@@ -339,7 +339,12 @@ __global__ void __launch_bounds__(kKnnMaxThreads, knn_min_blocks(F64, KMAX))
                     // second step for up to 16 slots and every fourth for 32
                     // (measured at 1M: on every step, k = 10 0.70 vs 0.57 ms;
                     // for 32 slots on every step, 2x slower; never, 1.2-1.5x
-                    // slower at k = 20..32)
+                    // slower at k = 20..32).  While the list fills, the
+                    // candidate passes every empty (+inf) slot above its
+                    // place; a separate fill branch that starts it at the
+                    // first empty slot was slower (uniform / clustered k = 10:
+                    // 0.526 / 0.955 -> 0.685 / 1.087 ms: divergence) and made
+                    // the 24- and 32-slot forms spill.
                     kd[KMAX - 1] = d2;
                     ki[KMAX - 1] = pidx;
 #pragma unroll
