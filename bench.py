@@ -258,10 +258,13 @@ def weight_pair_bounds(rates, mix, overhead: float = 0.0):
             "joint_limit": best[3], "split": {"exp2_on_fma": xe, "lg2_on_fma": xl}}
 
 
-def weight_roofline(pairs_per_launch, ms_per_launch, rates, mix, sms, mhz, traffic=None):
+def weight_roofline(pairs_per_launch, ms_per_launch, rates, mix, sms, mhz, traffic=None,
+                    loop=None):
     """Roofline record of the float32 weighting kernel (Gpair/s).  `peak` is
     the kernel's own-mix ceiling; the line also states the fraction of the
-    best-split ceiling and of the both-on-SFU ceiling."""
+    best-split ceiling and of the both-on-SFU ceiling, and (loop) the rate
+    of the kernel's inner loop run alone (aidw_probe_weight_loop) beside the
+    kernel's own rate per SM per clock."""
     b = weight_pair_bounds(rates, mix)
     scale = sms * mhz * 1e6 / 1e9
     achieved = pairs_per_launch / (ms_per_launch / 1000.0) / 1e9 if ms_per_launch else None
@@ -269,6 +272,18 @@ def weight_roofline(pairs_per_launch, ms_per_launch, rates, mix, sms, mhz, traff
 
     def frac(p):
         return achieved / p if achieved else None
+    replica = None
+    if loop and achieved:
+        per_clk = achieved / scale
+        replica = {"kernel_pairs_per_sm_clk": per_clk,
+                   "loop_alone_pairs_per_sm_clk": loop,
+                   "kernel_over_loop_alone": {c: (per_clk / r if r else None)
+                                              for c, r in loop.items()},
+                   "basis": "aidw_probe_weight_loop: the kernel's compiled inner loop over a "
+                            "shared-memory tile filled once (no copies, waits or barriers), "
+                            "at 2 CTAs per SM (the kernel's 128-register form) and 3 (an "
+                            "80-register form), clock64-timed; the kernel's rate at the "
+                            f"{mhz:.0f} MHz of the roofline"}
     return {"bound": "alu", "kernel": "k_weight_f32 (all-points weighting, Eq. 1)",
             "achieved": achieved, "peak": peak, "unit": "Gpair/s", "frac": frac(peak),
             "peak_joint": b["joint"] * scale, "frac_joint": frac(b["joint"] * scale),
@@ -283,7 +298,7 @@ def weight_roofline(pairs_per_launch, ms_per_launch, rates, mix, sms, mhz, traff
                            f"joint: best split (exp2 {b['joint_split']['exp2_on_fma']:.3f}, "
                            f"log2 {b['joint_split']['lg2_on_fma']:.3f}) = {b['joint']:.2f} "
                            f"limited by {b['joint_limit']}; sfu_both = {b['sfu_both']:.2f}"),
-            "pipe_rates_per_sm_clk": rates, "mix": mix}
+            "pipe_rates_per_sm_clk": rates, "mix": mix, "loop_alone": replica}
 
 
 # Algorithmic DRAM bytes of the two memory-side stages (compulsory traffic:
@@ -457,6 +472,12 @@ class Ctx:
         self.hbm = float(peaks.get("hbm_gbs", 6800.0))
         self.rates = binding.aidw_probe_pipe_rates()
         self.mix = binding.aidw_weight_mix()
+        self.loop = {}
+        for c in (2, 3):
+            try:
+                self.loop[f"{c}_ctas_per_sm"] = binding.aidw_probe_weight_loop(c)
+            except binding.AidwError:
+                self.loop[f"{c}_ctas_per_sm"] = None
 
     def tensors(self, w):
         return {k: self.torch.from_numpy(getattr(w, k)).to(self.dev)
@@ -501,7 +522,7 @@ class Ctx:
     def weight_roofline(self, stage, pairs_per_launch, traffic=None):
         w_ms, w_l = stage["weight"]
         return weight_roofline(pairs_per_launch, w_ms / w_l if w_l else None, self.rates,
-                               self.mix, self.sms, self.sm_mhz, traffic)
+                               self.mix, self.sms, self.sm_mhz, traffic, self.loop)
 
 
 def single_record(ctx, w, params, steps, warmup, cpu_seconds, seed, label, keep=None):

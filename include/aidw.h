@@ -417,6 +417,21 @@ aidw_status aidw_profile_read(double *ms, int64_t *launches);
 aidw_status aidw_probe_pipe_rates(double *lg2_per_sm_clk, double *ex2_per_sm_clk,
                                   double *ffma2_lanes_per_sm_clk);
 
+/* Measures, on the current device, the rate (query/data pairs per SM per
+ * clock) that the float32 weighting kernel's inner loop reaches when it runs
+ * alone: the same compiled loop (default split: 2 of 8 exp2 on the FMA
+ * pipe, 4 queries per thread, 256 threads) over a shared-memory tile filled
+ * once, with no bulk copies, waits or barriers, ctas_per_sm (2: the kernel's
+ * 128-register form; 3: an 80-register form) CTAs on every SM for ~1 ms,
+ * timed with clock64() (independent of the clock speed).  The kernel's own
+ * rate divided by this one tells how much its data pipeline and scheduling
+ * lose against what its instruction mix allows.  Synchronous; allocates a
+ * few KB of device memory for the duration of the call.  Returns
+ * AIDW_ERR_INVALID_ARG for another ctas_per_sm or a NULL output, and
+ * AIDW_ERR_CUDA if that many CTAs do not fit on an SM.  Measurement helper
+ * with no counterpart in the paper. */
+aidw_status aidw_probe_weight_loop(int ctas_per_sm, double *pairs_per_sm_clk);
+
 /* Instruction mix of the float32 weighting loop (AIDW_FP32_COMP) that this
  * library launches, for roofline accounting (no counterpart in the paper).
  * Every (query, data point) pair needs one log2 and one exp2; of every

@@ -134,6 +134,8 @@ def load(path: str | None = None):
         lib.aidw_profile_read.argtypes = [P(ctypes.c_double), P(ctypes.c_int64)]
         lib.aidw_probe_pipe_rates.restype = c_int
         lib.aidw_probe_pipe_rates.argtypes = [P(ctypes.c_double)] * 3
+        lib.aidw_probe_weight_loop.restype = c_int
+        lib.aidw_probe_weight_loop.argtypes = [c_int, P(ctypes.c_double)]
         lib.aidw_interpolate_host.restype = c_int
         lib.aidw_interpolate_host.argtypes = [vp, vp, vp, i64, vp, vp, i64, P(CParams), vp, vp, vp]
         lib.aidw_shard_range.restype = c_int
@@ -410,6 +412,15 @@ def aidw_probe_pipe_rates() -> dict:
     r = [ctypes.c_double() for _ in range(3)]
     _check(load().aidw_probe_pipe_rates(*(ctypes.byref(v) for v in r)), "aidw_probe_pipe_rates")
     return {"lg2": r[0].value, "ex2": r[1].value, "ffma2_lanes": r[2].value}
+
+
+def aidw_probe_weight_loop(ctas_per_sm: int = 2) -> float:
+    """Pairs per SM per clock of the float32 weighting loop run alone (no
+    copies, waits or barriers) at 2 or 3 CTAs per SM."""
+    r = ctypes.c_double()
+    _check(load().aidw_probe_weight_loop(int(ctas_per_sm), ctypes.byref(r)),
+           "aidw_probe_weight_loop")
+    return r.value
 
 
 def aidw_weight_mix() -> dict:

@@ -48,6 +48,7 @@
 
 #include "aidw_device.cuh"
 #include "aidw_internal.cuh"
+#include "weight_loop.cuh"
 
 namespace aidw {
 
@@ -56,16 +57,6 @@ namespace {
 constexpr int kDTile = 2048;   // points per shared-memory stage
 static_assert(kDTile == kWeightTile, "weighting tiles are staged whole");
 constexpr int kStages = 3;
-// Points per plain float32 partial sum (per lane) before it is folded into
-// the TwoSum-compensated total.  A plain sum of n positive terms is within
-// (n - 1) * 2^-24 of its magnitude, so with 64 the error budget of a
-// prediction (numerator and denominator) stays under 2 * 63 * 2^-24 = 7.5e-6
-// of S_q (the normalised measure) plus the SFU approximation errors, inside
-// the 1e-5 bound; measured on GB300 at n = m = 1M (weighting ms, unroll of
-// the point loop): chunk 32 / unroll 4: 352.3, 64 / 4: 345.4, 64 / 8:
-// 341.6, 64 / 16: 334.5, 64 / 32: 389.3, 32 / 16: 346.9, 16 / 4: 367.0.
-constexpr int kChunk = 64;
-constexpr int kChunk2 = 2 * kChunk;
 constexpr int kWaitTries = 2000;  // tries of up to ~1 ms: a data-tile wait gives up after ~2 s
 
 template <bool F64>
@@ -300,47 +291,7 @@ __global__ void __launch_bounds__(THREADS, MINB)
                     F2 ps[Q], pz[Q];
 #pragma unroll
                     for (int i = 0; i < Q; ++i) ps[i] = pz[i] = zero2;
-#pragma unroll 16
-                    for (int st = 0; st < kChunk2 / 4; ++st) {
-                        // steps alternate between PE and PE2 exp2 products on the
-                        // FMA pipe (the parity is a constant in each unrolled copy)
-                        const int pe = (st & 1) ? PE2 : PE;
-                        const int jj = c0 + 4 * st;
-                        const float4 xv = *reinterpret_cast<const float4 *>(X + jj);
-                        const float4 yv = *reinterpret_cast<const float4 *>(Y + jj);
-                        const float4 zv = *reinterpret_cast<const float4 *>(Z + jj);
-                        const F2 xs[2] = {f2_pack(xv.x, xv.y), f2_pack(xv.z, xv.w)};
-                        const F2 ys[2] = {f2_pack(yv.x, yv.y), f2_pack(yv.z, yv.w)};
-                        const F2 zs[2] = {f2_pack(zv.x, zv.y), f2_pack(zv.z, zv.w)};
-#pragma unroll
-                        for (int h = 0; h < 2; ++h) {
-#pragma unroll
-                            for (int i = 0; i < Q; ++i) {
-                                const F2 dx = f2_add(qx2[i], xs[h]);
-                                const F2 dy = f2_add(qy2[i], ys[h]);
-                                const F2 d2 = f2_fma(dy, dy, f2_mul(dx, dx));
-                                F2 lg;
-                                if (h * Q + i >= 2 * Q - PL) {
-                                    lg = f2_log2_poly(d2);
-                                } else {
-                                    float d0, d1;
-                                    f2_unpack(d2, d0, d1);
-                                    lg = f2_pack(lg2_sfu(d0), lg2_sfu(d1));
-                                }
-                                const F2 tt = f2_fma(lg, c2[i], b2[i]);
-                                F2 w;
-                                if (h * Q + i < pe) {
-                                    w = f2_exp2_poly(tt);
-                                } else {
-                                    float t0, t1;
-                                    f2_unpack(tt, t0, t1);
-                                    w = f2_pack(ex2_sfu(t0), ex2_sfu(t1));
-                                }
-                                ps[i] = f2_add(ps[i], w);
-                                pz[i] = f2_fma(w, zs[h], pz[i]);
-                            }
-                        }
-                    }
+                    weight_chunk_f32<Q, PE, PL, PE2>(X, Y, Z, c0, qx2, qy2, c2, b2, ps, pz);
 #pragma unroll
                     for (int i = 0; i < Q; ++i) {
                         f2_comp_add(hw[i], lw[i], ps[i]);

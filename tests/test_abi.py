@@ -199,3 +199,12 @@ def test_entry_points_open_and_close_named_nvtx_ranges(lib, tmp_path):
     assert log.read_text().split("\n")[:-1] == [
         "push aidw_interpolate_host", "pop", "push aidw_interpolate_shard", "pop",
         "push aidw_batch_run", "pop"]
+
+
+def test_weight_loop_probe_checks_arguments_without_a_gpu(lib):
+    """aidw_probe_weight_loop takes 2 or 3 CTAs per SM and a non-NULL output,
+    checked before any CUDA call."""
+    d = ctypes.c_double(-1.0)
+    assert lib.aidw_probe_weight_loop(4, ctypes.byref(d)) == 1
+    assert lib.aidw_probe_weight_loop(1, ctypes.byref(d)) == 1
+    assert lib.aidw_probe_weight_loop(2, None) == 1

@@ -207,6 +207,19 @@ def test_pipe_rate_probe(aidw):
     assert r["ex2"] >= 0.9 * r["lg2"]
 
 
+def test_weight_loop_probe(aidw):
+    """The weighting loop run alone: a positive rate no faster than its SFU
+    ceiling allows (one lg2 and at least 3/4 of an ex2 per pair on the SFU),
+    and argument checks."""
+    r = aidw.aidw_probe_pipe_rates()
+    ceiling = 1.0 / (1.0 / r["lg2"] + 0.75 / r["ex2"])
+    for c in (2, 3):
+        v = aidw.aidw_probe_weight_loop(c)
+        assert 0.3 * ceiling < v <= 1.02 * ceiling, (c, v, ceiling)
+    with pytest.raises(aidw.AidwError):
+        aidw.aidw_probe_weight_loop(4)
+
+
 @pytest.mark.slow
 def test_precision_form_4M_sampled(aidw, oracle):
     """n = m = 4,194,304 uniform in [0,1000]^2: float32-compensated path on
