@@ -344,7 +344,12 @@ __global__ void __launch_bounds__(kKnnMaxThreads, knn_min_blocks(F64, KMAX))
                     // place; a separate fill branch that starts it at the
                     // first empty slot was slower (uniform / clustered k = 10:
                     // 0.526 / 0.955 -> 0.685 / 1.087 ms: divergence) and made
-                    // the 24- and 32-slot forms spill.
+                    // the 24- and 32-slot forms spill.  An insertion without
+                    // a chain (rank from independent compares, then every
+                    // slot above it shifted by independent selects) was
+                    // slower for 24 and 32 slots (clustered k = 24 / 32,
+                    // uniform k = 32: 1.81 / 2.56 / 1.67 -> 2.59 / 3.91 /
+                    // 2.49 ms): the bubble's early exit saves more.
                     kd[KMAX - 1] = d2;
                     ki[KMAX - 1] = pidx;
 #pragma unroll
