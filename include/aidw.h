@@ -432,6 +432,27 @@ aidw_status aidw_probe_pipe_rates(double *lg2_per_sm_clk, double *ex2_per_sm_clk
  * with no counterpart in the paper. */
 aidw_status aidw_probe_weight_loop(int ctas_per_sm, double *pairs_per_sm_clk);
 
+/* Index checks of the bounds-checked build of this library
+ * (libaidw_checked.so, built with -DAIDW_BOUNDS_CHECK; no GPU memory checker
+ * can run here).  In that build the kernels test the indices they compute
+ * (cells of points and queries, cell heads, scatter and fix-up
+ * destinations, ring segments of the kNN, the source range of every
+ * weighting tile copy) against the sizes of the arrays they index; a failed
+ * test skips the access and is counted.  This call waits for the device,
+ * then reports: *checked_build 1 in the checked build, 0 in the normal one
+ * (whose kernels carry no checks); *violations the number of failed tests
+ * since the library was loaded; *first the first one as (site << 48 |
+ * index), or all ones if none.  Any pointer may be NULL.  Measurement and
+ * test helper with no counterpart in the paper. */
+aidw_status aidw_bounds_report(int *checked_build, uint64_t *violations, uint64_t *first);
+
+/* Test hook of the index checks: one GPU thread evaluates the check of the
+ * checked build on `index` against [0, n) (the test accesses no memory) and
+ * writes 1 (in range) or 0 to *in_range (may be NULL).  In the checked build
+ * a value out of range is recorded like a kernel's failed check (site 12);
+ * in the normal build the check is the constant true.  Synchronous. */
+aidw_status aidw_test_bounds_check(int64_t index, int64_t n, int *in_range);
+
 /* Instruction mix of the float32 weighting loop (AIDW_FP32_COMP) that this
  * library launches, for roofline accounting (no counterpart in the paper).
  * Every (query, data point) pair needs one log2 and one exp2; of every

@@ -18,6 +18,8 @@ from dataclasses import dataclass, field
 
 PKG = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(PKG, "libaidw.so")
+# the bounds-checked build of the same sources (build(checked=True))
+LIB_CHECKED_PATH = os.path.join(PKG, "libaidw_checked.so")
 
 AIDW_OK = 0
 AIDW_FP32_COMP = 0
@@ -143,6 +145,10 @@ def load(path: str | None = None):
         lib.aidw_interpolate_shard.restype = c_int
         lib.aidw_interpolate_shard.argtypes = [vp, vp, vp, i64, c_int, c_int, P(CParams), vp,
                                                vp, vp]
+        lib.aidw_bounds_report.restype = c_int
+        lib.aidw_bounds_report.argtypes = [P(c_int), P(ctypes.c_uint64), P(ctypes.c_uint64)]
+        lib.aidw_test_bounds_check.restype = c_int
+        lib.aidw_test_bounds_check.argtypes = [i64, i64, P(c_int)]
         lib.aidw_weight_mix.restype = c_int
         lib.aidw_weight_mix.argtypes = [P(c_int), P(c_int), P(c_int), P(ctypes.c_double),
                                         P(ctypes.c_double)]
@@ -421,6 +427,26 @@ def aidw_probe_weight_loop(ctas_per_sm: int = 2) -> float:
     _check(load().aidw_probe_weight_loop(int(ctas_per_sm), ctypes.byref(r)),
            "aidw_probe_weight_loop")
     return r.value
+
+
+def aidw_bounds_report() -> dict:
+    """Index-check record of the loaded library: whether it is the checked
+    build, how many checks failed since it was loaded, and the site and
+    index of the first failure (None if none)."""
+    c, v, f = ctypes.c_int(), ctypes.c_uint64(), ctypes.c_uint64()
+    _check(load().aidw_bounds_report(ctypes.byref(c), ctypes.byref(v), ctypes.byref(f)),
+           "aidw_bounds_report")
+    first = None if f.value == (1 << 64) - 1 else (f.value >> 48, f.value & ((1 << 48) - 1))
+    return {"checked_build": bool(c.value), "violations": v.value, "first": first}
+
+
+def aidw_test_bounds_check(index: int, n: int) -> bool:
+    """Evaluates one index check on the GPU (no memory behind it); in the
+    checked build an index outside [0, n) is recorded as a failure."""
+    r = ctypes.c_int()
+    _check(load().aidw_test_bounds_check(int(index), int(n), ctypes.byref(r)),
+           "aidw_test_bounds_check")
+    return bool(r.value)
 
 
 def aidw_weight_mix() -> dict:

@@ -4,6 +4,11 @@ Each ``csrc/*.cu`` translation unit is compiled in parallel with nvcc
 (``-gencode arch=compute_103a,code=sm_103a``), then linked into one shared
 library next to this file.  A content hash of the sources and flags names
 the build, so an unchanged tree is not rebuilt.
+
+``build(checked=True)`` builds the same sources with -DAIDW_BOUNDS_CHECK
+into ``libaidw_checked.so``: the kernels test the indices they compute
+against their arrays and count failures (``aidw_bounds_report``), the
+stand-in for a GPU memory checker.
 """
 from __future__ import annotations
 
@@ -20,6 +25,8 @@ CSRC = os.path.join(PKG, "csrc")
 INCLUDE = os.path.join(ROOT, "include")
 BUILD = os.path.join(PKG, "_build")
 LIB = os.path.join(PKG, "libaidw.so")
+LIB_CHECKED = os.path.join(PKG, "libaidw_checked.so")
+CHECKED_FLAGS = ["-DAIDW_BOUNDS_CHECK"]
 
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC_FLAGS = ["-O3", "-lineinfo", "-std=c++17", "--ftz=true", "--prec-div=true",
@@ -38,7 +45,7 @@ def _sources():
     return sorted(glob.glob(os.path.join(CSRC, "*.cu")))
 
 
-def _tag() -> str:
+def _tag(extra_flags=()) -> str:
     h = hashlib.sha1()
     files = _sources() + sorted(glob.glob(os.path.join(CSRC, "*.cuh"))) + \
         sorted(glob.glob(os.path.join(INCLUDE, "*.h")))
@@ -46,7 +53,7 @@ def _tag() -> str:
         h.update(os.path.basename(f).encode())
         with open(f, "rb") as fh:
             h.update(fh.read())
-    h.update(" ".join(ARCH + NVCC_FLAGS).encode())
+    h.update(" ".join(ARCH + NVCC_FLAGS + list(extra_flags)).encode())
     return h.hexdigest()[:16]
 
 
@@ -56,21 +63,26 @@ def _compile(src: str, obj: str, extra: list[str]) -> tuple[str, int, str]:
     return src, r.returncode, r.stdout + r.stderr
 
 
-def build(force: bool = False, verbose: bool = False, ptxas_info: bool = False) -> str:
-    """Compile and link libaidw.so; returns its path."""
-    tag = _tag()
-    stamp = os.path.join(BUILD, "stamp")
-    if not force and os.path.exists(LIB) and os.path.exists(stamp):
+def build(force: bool = False, verbose: bool = False, ptxas_info: bool = False,
+          checked: bool = False) -> str:
+    """Compile and link libaidw.so (libaidw_checked.so if checked); returns
+    its path."""
+    flags = CHECKED_FLAGS if checked else []
+    lib = LIB_CHECKED if checked else LIB
+    bdir = os.path.join(BUILD, "checked") if checked else BUILD
+    tag = _tag(flags)
+    stamp = os.path.join(bdir, "stamp")
+    if not force and os.path.exists(lib) and os.path.exists(stamp):
         with open(stamp) as f:
             if f.read().strip() == tag:
-                return LIB
-    os.makedirs(BUILD, exist_ok=True)
-    extra = ["-Xptxas", "-v"] if ptxas_info else []
+                return lib
+    os.makedirs(bdir, exist_ok=True)
+    extra = flags + (["-Xptxas", "-v"] if ptxas_info else [])
     objs = []
     jobs = []
     with cf.ThreadPoolExecutor(max_workers=max(1, min(8, os.cpu_count() or 1))) as ex:
         for src in _sources():
-            obj = os.path.join(BUILD, os.path.basename(src)[:-3] + ".o")
+            obj = os.path.join(bdir, os.path.basename(src)[:-3] + ".o")
             objs.append(obj)
             jobs.append(ex.submit(_compile, src, obj, extra))
         errors = []
@@ -82,17 +94,18 @@ def build(force: bool = False, verbose: bool = False, ptxas_info: bool = False) 
                 errors.append(src)
     if errors:
         raise RuntimeError("nvcc failed for " + ", ".join(os.path.basename(e) for e in errors))
-    tmp = LIB + ".tmp"
+    tmp = lib + ".tmp"
     cmd = [nvcc(), *ARCH, "-shared", "-cudart", "static", "-o", tmp, *objs]
     r = subprocess.run(cmd, capture_output=True, text=True)
     if r.returncode:
         raise RuntimeError("link failed:\n" + r.stdout + r.stderr)
-    os.replace(tmp, LIB)
+    os.replace(tmp, lib)
     with open(stamp, "w") as f:
         f.write(tag + "\n")
-    return LIB
+    return lib
 
 
 if __name__ == "__main__":
     import sys
-    print(build(force="--force" in sys.argv, verbose=True, ptxas_info="--ptxas" in sys.argv))
+    print(build(force="--force" in sys.argv, verbose=True, ptxas_info="--ptxas" in sys.argv,
+                checked="--checked" in sys.argv))

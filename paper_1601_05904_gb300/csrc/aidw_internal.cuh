@@ -6,6 +6,7 @@
 #include <stdint.h>
 
 #include "aidw.h"
+#include "bounds.cuh"
 
 namespace aidw {
 

@@ -13,6 +13,23 @@
 
 namespace aidw {
 
+namespace bounds {
+// Readers of the index-check records of every translation unit (registered
+// at load time by the checked build; empty in the normal build).
+static std::mutex g_readers_mu;
+static std::vector<Reader> &readers()
+{
+    static std::vector<Reader> v;
+    return v;
+}
+bool add_reader(Reader r)
+{
+    std::lock_guard<std::mutex> lk(g_readers_mu);
+    readers().push_back(r);
+    return true;
+}
+}  // namespace bounds
+
 aidw_status cuda_status(cudaError_t e)
 {
     if (e == cudaSuccess) return AIDW_OK;
@@ -625,6 +642,31 @@ aidw_status aidw_profile_read(double *ms, int64_t *launches)
         g_ev_pool.push_back(r.b);
     }
     return st;
+}
+
+aidw_status aidw_bounds_report(int *checked_build, uint64_t *violations, uint64_t *first)
+{
+    using namespace aidw::bounds;
+    std::vector<Reader> rs;
+    {
+        std::lock_guard<std::mutex> lk(g_readers_mu);
+        rs = readers();
+    }
+    if (checked_build) *checked_build = rs.empty() ? 0 : 1;
+    unsigned long long total = 0, f = ~0ull;
+    if (!rs.empty() && cudaDeviceSynchronize() != cudaSuccess) {
+        cudaGetLastError();
+        return AIDW_ERR_CUDA;
+    }
+    for (Reader r : rs) {
+        unsigned long long c = 0, fi = ~0ull;
+        r(&c, &fi);
+        total += c;
+        if (f == ~0ull) f = fi;
+    }
+    if (violations) *violations = total;
+    if (first) *first = f;
+    return AIDW_OK;
 }
 
 }  // extern "C"

@@ -113,7 +113,7 @@ __global__ void __launch_bounds__(kThreads) k_b_scatter(const BJob *__restrict__
     const BJob &J = jobs[job_of_block<&BJob::blk_pt>(jobs, n_jobs, blockIdx.x)];
     const long long i = (blockIdx.x - J.blk_pt) * kThreads + threadIdx.x;
     if (i >= J.n || grid_failed(J.g)) return;
-    scatter_point(i, J.x, J.y, J.z, J.start, J.key, J.rank, J.tmp);
+    scatter_point(i, J.x, J.y, J.z, J.start, J.key, J.rank, J.tmp, J.g, J.n);
 }
 
 __global__ void __launch_bounds__(kThreads) k_b_fixup_pad(const BJob *__restrict__ jobs,
@@ -122,7 +122,7 @@ __global__ void __launch_bounds__(kThreads) k_b_fixup_pad(const BJob *__restrict
     const BJob &J = jobs[job_of_block<&BJob::blk_fp>(jobs, n_jobs, blockIdx.x)];
     const long long s = (blockIdx.x - J.blk_fp) * kThreads + threadIdx.x;
     if (s < J.n) {
-        if (!grid_failed(J.g)) fixup_one(s, J.g, J.start, J.tmp, J.pts, J.perm, J.wt);
+        if (!grid_failed(J.g)) fixup_one(s, J.g, J.start, J.tmp, J.pts, J.perm, J.wt, J.n);
     } else if (s < (J.n_pad > J.n_wpad ? J.n_pad : J.n_wpad)) {
         pad_one(s, J.n_pad, J.n_wpad, J.pts, J.wt);
     }
@@ -150,7 +150,7 @@ __global__ void __launch_bounds__(kThreads) k_b_qscatter(const BJob *__restrict_
     const BJob &J = jobs[job_of_block<&BJob::blk_q>(jobs, n_jobs, blockIdx.x)];
     const long long i = (blockIdx.x - J.blk_q) * kThreads + threadIdx.x;
     if (i >= J.m || grid_failed(J.g)) return;
-    scatter_one(i, J.qcount, J.qkey, J.qrank, J.qorder);
+    scatter_one(i, J.qcount, J.qkey, J.qrank, J.qorder, J.m);
 }
 
 __global__ void k_b_status(const BJob *__restrict__ jobs, int n_jobs, int *status)

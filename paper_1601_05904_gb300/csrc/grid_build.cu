@@ -74,7 +74,7 @@ __global__ void __launch_bounds__(kThreads) k_scatter(const float *__restrict__ 
 {
     const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n || grid_failed(g)) return;
-    scatter_point(i, x, y, z, start, key, rank, tmp);
+    scatter_point(i, x, y, z, start, key, rank, tmp, g, n);
 }
 
 __global__ void __launch_bounds__(kThreads) k_fixup_pad(long long n, long long pad_hi,
@@ -88,7 +88,7 @@ __global__ void __launch_bounds__(kThreads) k_fixup_pad(long long n, long long p
 {
     const long long s = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (s < n) {
-        if (!grid_failed(g)) fixup_one(s, g, start, tmp, pts, perm, wt);
+        if (!grid_failed(g)) fixup_one(s, g, start, tmp, pts, perm, wt, n);
     } else if (s < pad_hi) {
         pad_one(s, n_pad, n_wpad, pts, wt);
     }

@@ -228,7 +228,7 @@ __device__ __forceinline__ void key_one_xy(long long i, float x, float y, const 
 {
     const int c = cell_index(x, y, g);
     key[i] = c;
-    rank[i] = atomicAdd(count + c, 1);
+    rank[i] = AIDW_IN(c, g->n_cells, bounds::kKeyCell) ? atomicAdd(count + c, 1) : 0;
 }
 
 // Cell of data point i and its (unstable) rank among the points of that cell.
@@ -361,9 +361,12 @@ __device__ __forceinline__ void scan_lookback_block(int *__restrict__ a, long lo
 
 __device__ __forceinline__ void scatter_one(long long i, const int *__restrict__ start,
                                             const int *__restrict__ key,
-                                            const int *__restrict__ rank, int *__restrict__ tmp)
+                                            const int *__restrict__ rank, int *__restrict__ tmp,
+                                            long long n_out)
 {
-    tmp[start[key[i]] + rank[i]] = (int)i;
+    const int dest = start[key[i]] + rank[i];
+    if (!AIDW_IN(dest, n_out, bounds::kScatterDest)) return;
+    tmp[dest] = (int)i;
 }
 
 // Data point i goes to its cell's segment (in arrival order) as a whole
@@ -376,14 +379,19 @@ __device__ __forceinline__ void scatter_point(long long i, const float *__restri
                                               const int *__restrict__ start,
                                               const int *__restrict__ key,
                                               const int *__restrict__ rank,
-                                              Point *__restrict__ tmp)
+                                              Point *__restrict__ tmp,
+                                              const GridDev *__restrict__ g, long long n)
 {
+    const int c = key[i];
+    if (!AIDW_IN(c, g->n_cells, bounds::kScatterHead)) return;
+    const int dest = start[c] + rank[i];
+    if (!AIDW_IN(dest, n, bounds::kScatterDest)) return;
     Point p;
     p.x = x[i];
     p.y = y[i];
     p.z = z[i];
     p.idx = (int)i;
-    tmp[start[key[i]] + rank[i]] = p;
+    tmp[dest] = p;
 }
 
 // Position s holds some point i of cell c (recomputed from its coordinates
@@ -393,15 +401,19 @@ __device__ __forceinline__ void scatter_point(long long i, const float *__restri
 __device__ __forceinline__ void fixup_one(long long s, const GridDev *__restrict__ g,
                                           const int *__restrict__ start,
                                           const Point *__restrict__ tmp, Point *__restrict__ pts,
-                                          int *__restrict__ perm, float *__restrict__ wt)
+                                          int *__restrict__ perm, float *__restrict__ wt,
+                                          long long n)
 {
     const Point p = tmp[s];
     const int i = p.idx;
     const int c = cell_index(p.x, p.y, g);
+    if (!AIDW_IN(c, g->n_cells, bounds::kFixupHead)) return;
     const int a = start[c], b = start[c + 1];
+    if (!AIDW_IN(b - 1, n, bounds::kFixupSegment)) return;
     int r = 0;
     for (int t = a; t < b; ++t) r += (tmp[t].idx < i);
     const long long pos = (long long)a + r;
+    if (!AIDW_IN(pos, n, bounds::kFixupDest)) return;
     pts[pos] = p;
     perm[pos] = i;
     float *tile = wt + (pos / kWeightTile) * (3 * kWeightTile) + pos % kWeightTile;

@@ -227,6 +227,7 @@ __global__ void __launch_bounds__(kKnnMaxThreads, knn_min_blocks(F64, KMAX))
     const bool failed = (g->status & (kStatusNonfiniteData | kStatusCapacity)) != 0;
     const long long li = gq - J.q_base;
     const long long q = (J.order && !failed) ? (long long)J.order[li] : li;
+    if (!AIDW_IN(q, J.nq, bounds::kKnnOrder)) return;
     const Point *__restrict__ pts = J.pts;
     const int *__restrict__ start = J.start;
     const int k = J.k;
@@ -319,7 +320,11 @@ __global__ void __launch_bounds__(kKnnMaxThreads, knn_min_blocks(F64, KMAX))
                 ca = cb = right ? col + L : col - L;
             }
             const long long base = (long long)r * nc;
+            if (!AIDW_IN(base + ca, g->n_cells + 1, bounds::kKnnHead) ||
+                !AIDW_IN(base + cb + 1, g->n_cells + 1, bounds::kKnnHead))
+                continue;
             const int a = start[base + ca], b = start[base + cb + 1];
+            if (!AIDW_IN(b, g->n_data + 1, bounds::kKnnPoints)) continue;
             found += b - a;
             // the next point's load is issued before the current one is
             // tested, so its L2 latency overlaps the top-k update (kNN ms at
@@ -420,6 +425,8 @@ __global__ void __launch_bounds__(kKnnMaxThreads, knn_min_blocks(F64, KMAX))
         HitSum<F64> hits;
         for (int r = max(row - R, 0); r <= min(row + R, nr - 1); ++r) {
             const long long base = (long long)r * nc;
+            if (!AIDW_IN(base + min(col + R, nc - 1) + 1, g->n_cells + 1, bounds::kKnnHead))
+                continue;
             const int a = start[base + max(col - R, 0)], b = start[base + min(col + R, nc - 1) + 1];
             for (int s = a; s < b; ++s) {
                 const float4 p = reinterpret_cast<const float4 *>(pts)[s];
@@ -531,6 +538,7 @@ __global__ void __launch_bounds__(kKnnMaxThreads)
     const bool failed = (g->status & (kStatusNonfiniteData | kStatusCapacity)) != 0;
     const long long li = gq - J.q_base;
     const long long q = (J.order && !failed) ? (long long)J.order[li] : li;
+    if (!AIDW_IN(q, J.nq, bounds::kKnnOrder)) return;
     const Point *__restrict__ pts = J.pts;
     const int *__restrict__ start = J.start;
     const int k = J.k;
@@ -604,7 +612,11 @@ __global__ void __launch_bounds__(kKnnMaxThreads)
                 ca = cb = right ? col + L : col - L;
             }
             const long long base = (long long)r * nc;
+            if (!AIDW_IN(base + ca, g->n_cells + 1, bounds::kKnnHead) ||
+                !AIDW_IN(base + cb + 1, g->n_cells + 1, bounds::kKnnHead))
+                continue;
             const int a = start[base + ca], b = start[base + cb + 1];
+            if (!AIDW_IN(b, g->n_data + 1, bounds::kKnnPoints)) continue;
             found += b - a;
             for (int s0 = a; s0 < b; s0 += 32) {
                 const int s = s0 + lane;
@@ -829,7 +841,7 @@ __global__ void __launch_bounds__(gridk::kThreads)
                const int *__restrict__ rank, int *__restrict__ order)
 {
     const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i < nq) order[start[key[i]] + rank[i]] = (int)i;
+    if (i < nq) gridk::scatter_one(i, start, key, rank, order, nq);
 }
 
 // Whether the single-grid kNN sorts its queries by cell (AIDW_KNN_SORT=0|1

@@ -137,8 +137,31 @@ __global__ void __launch_bounds__(256, MINB) k_probe_loop(float *out, long long 
     out[(long long)blockIdx.x * blockDim.x + threadIdx.x] = s;
 }
 
+// One check of the checked build's kind, with no access behind it.
+__global__ void k_bounds_hook(long long index, long long n, int *result)
+{
+    *result = AIDW_IN(index, n, bounds::kTestHook) ? 1 : 0;
+}
+
 }  // namespace
 }  // namespace aidw
+
+extern "C" aidw_status aidw_test_bounds_check(int64_t index, int64_t n, int *in_range)
+{
+    using namespace aidw;
+    int *d = nullptr;
+    if (cudaMalloc((void **)&d, sizeof(int)) != cudaSuccess) {
+        cudaGetLastError();
+        return AIDW_ERR_OOM;
+    }
+    k_bounds_hook<<<1, 1>>>((long long)index, (long long)n, d);
+    int r = 0;
+    cudaError_t e = cudaMemcpy(&r, d, sizeof(int), cudaMemcpyDeviceToHost);
+    cudaFree(d);
+    if (e != cudaSuccess) return cuda_status(e);
+    if (in_range) *in_range = r;
+    return AIDW_OK;
+}
 
 extern "C" aidw_status aidw_probe_weight_loop(int ctas_per_sm, double *pairs_per_sm_clk)
 {

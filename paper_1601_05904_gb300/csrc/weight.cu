@@ -187,6 +187,9 @@ __device__ __forceinline__ void issue_tile_soa(const SKArgs &a, float *buf, uint
     // piece d is piece (d mod 2^sh) of weighting tile (d >> sh); pieces are
     // multiples of kChunk2 points, so every copy starts 512-byte aligned
     const long long piece = kDTile >> sh;
+    if (!AIDW_IN(d >> sh, (J.n_data + kDTile - 1) / kDTile, bounds::kWeightTile) ||
+        !AIDW_IN((d & ((1LL << sh) - 1)) * piece + bytes / 4 - 1, kDTile, bounds::kWeightPiece))
+        return;  // (checked build) the copy is skipped; the consumer's bounded wait expires
     const float *src = J.wt + (d >> sh) * (3 * kDTile) + (d & ((1LL << sh) - 1)) * piece;
     mbar_expect_tx(bar, 3u * bytes);
     bulk_g2s(buf, src, bytes, bar);
@@ -202,6 +205,7 @@ __device__ __forceinline__ void issue_tile_aos(const SKArgs &a, Point *buf, uint
     const WJob J = job_of_unit(a, u);
     const long long d = (u - J.unit_base) % J.D;
     const uint32_t bytes = (uint32_t)aos_count(J.n_pad, d) * (uint32_t)sizeof(Point);
+    if (!AIDW_IN(d * kDTile + bytes / sizeof(Point) - 1, J.n_pad, bounds::kWeightPiece)) return;
     mbar_expect_tx(bar, bytes);
     bulk_g2s(buf, J.pts + d * kDTile, bytes, bar);
 }

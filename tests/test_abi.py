@@ -208,3 +208,23 @@ def test_weight_loop_probe_checks_arguments_without_a_gpu(lib):
     assert lib.aidw_probe_weight_loop(4, ctypes.byref(d)) == 1
     assert lib.aidw_probe_weight_loop(1, ctypes.byref(d)) == 1
     assert lib.aidw_probe_weight_loop(2, None) == 1
+
+
+def test_bounds_report_of_the_normal_build(lib):
+    """The normal build carries no index checks: the report says so, with
+    no failures, and needs no GPU."""
+    c, v, f = ctypes.c_int(-1), ctypes.c_uint64(7), ctypes.c_uint64(0)
+    assert lib.aidw_bounds_report(ctypes.byref(c), ctypes.byref(v), ctypes.byref(f)) == 0
+    assert c.value == 0 and v.value == 0 and f.value == (1 << 64) - 1
+    assert lib.aidw_bounds_report(None, None, None) == 0
+
+
+def test_checked_build_exports_every_symbol():
+    """The bounds-checked build of the same sources links and exports every
+    entry point include/aidw.h declares."""
+    if not shutil.which("nvcc") and not os.path.exists("/usr/local/cuda/bin/nvcc"):
+        pytest.skip("nvcc not available")
+    from paper_1601_05904_gb300 import build
+    checked = ctypes.CDLL(build.build(checked=True))
+    missing = [n for n in declared_functions() if not hasattr(checked, n)]
+    assert not missing, missing
