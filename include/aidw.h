@@ -437,7 +437,8 @@ aidw_status aidw_probe_weight_loop(int ctas_per_sm, double *pairs_per_sm_clk);
  * can run here).  In that build the kernels test the indices they compute
  * (cells of points and queries, cell heads, scatter and fix-up
  * destinations, ring segments of the kNN, the source range of every
- * weighting tile copy) against the sizes of the arrays they index; a failed
+ * weighting tile copy, the partial-sum slots of the weighting and its
+ * finalize) against the sizes of the arrays they index; a failed
  * test skips the access and is counted.  This call waits for the device,
  * then reports: *checked_build 1 in the checked build, 0 in the normal one
  * (whose kernels carry no checks); *violations the number of failed tests

@@ -199,7 +199,7 @@ int weight_resident_ctas(int device, bool fp64);
 aidw_status weight_launch_batch(const WJob *jobs, int n_jobs, long long total_u,
                                 long long total_q, bool fp64, void *part, long long G,
                                 const long long *bounds, int *status, int *fail, int device,
-                                cudaStream_t s);
+                                cudaStream_t s, long long n_slots);
 // Points of data tile d that the weighting kernel processes for a job of
 // n_data points (n_pad padded): the cost of one unit.
 long long weight_unit_points(long long n_data, long long n_pad, long long d, bool fp64);

@@ -353,7 +353,8 @@ aidw_status enqueue(aidw_batch_plan *P, cudaStream_t s, bool knn_only)
     }
     if (st != AIDW_OK || knn_only) return st;
     st = weight_launch_batch(P->d_wj, J, P->total_u, P->total_q, P->fp64, P->d_part, P->G,
-                             P->d_bounds, P->d_status, P->d_status + 1, P->device, s);
+                             P->d_bounds, P->d_status, P->d_status + 1, P->device, s,
+                             P->total_tiles + P->G);
     if (st != AIDW_OK) return st;
     k_b_status<<<jb, 128, 0, s>>>(P->d_bj, J, P->d_status);
     return cuda_status(cudaGetLastError());

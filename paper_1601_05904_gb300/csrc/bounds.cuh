@@ -29,6 +29,7 @@ enum Site : int {
     kWeightTile = 10,     // weighting tile of a unit, against the tiles of the grid
     kWeightPiece = 11,    // end of a unit's piece, against the tile length
     kTestHook = 12,       // aidw_test_bounds_check (no access behind it)
+    kWeightSlot = 13,     // stream-K partial-sum slot, against the slots of the launch
 };
 
 // Reads one translation unit's record (count, first = site << 48 | index).

@@ -101,6 +101,7 @@ struct SKArgs {
                               // increasing (cost-balanced, batched launches); or
                               // null for equal unit counts
     long long total_q;  // queries of all jobs
+    long long n_slots;  // partial-sum slots of the scratch array (query tiles + CTAs)
     int *status;
     int *fail;          // this launch's failure flag: zeroed before the launch, set by a
                         // CTA whose wait expired; the finalize then writes NaN
@@ -322,6 +323,7 @@ __global__ void __launch_bounds__(THREADS, MINB)
         }
 
         const long long slot = J.tile_base + t + cta;
+        if (!AIDW_IN(slot, a.n_slots, bounds::kWeightSlot)) continue;
 #pragma unroll
         for (int i = 0; i < Q; ++i) {
             float w0, w1, wl0, wl1, z0, z1, zl0, zl1;
@@ -360,6 +362,7 @@ __global__ void k_finalize_f32(SKArgs a, const float4 *__restrict__ part)
     const long long j0 = share_owner(a, ub), j1 = share_owner(a, ub + J.D - 1);
     float hw = 0.0f, lw = 0.0f, hz = 0.0f, lz = 0.0f;
     for (long long j = j0; j <= j1; ++j) {
+        if (!AIDW_IN(J.tile_base + t + j, a.n_slots, bounds::kWeightSlot)) break;
         const float4 v = part[(J.tile_base + t + j) * C::kQTile + l];
         comp_add(hw, lw, v.x);
         lw = add_rn(lw, v.y);
@@ -448,6 +451,7 @@ __global__ void __launch_bounds__(WCfg<true>::kThreads, WCfg<true>::kMinBlocks)
                 issue_tile_aos<HOOK>(a, buf + s * kDTile, &full[s], u + kStages);
         }
         const long long slot = J.tile_base + t + cta;
+        if (!AIDW_IN(slot, a.n_slots, bounds::kWeightSlot)) continue;
 #pragma unroll
         for (int i = 0; i < C::kQPT; ++i)
             part[slot * C::kQTile + (long long)i * C::kThreads + threadIdx.x] =
@@ -477,6 +481,7 @@ __global__ void k_finalize_f64(SKArgs a, const double2 *__restrict__ part)
     const long long j0 = share_owner(a, ub), j1 = share_owner(a, ub + J.D - 1);
     double sw = 0.0, swz = 0.0;
     for (long long j = j0; j <= j1; ++j) {
+        if (!AIDW_IN(J.tile_base + t + j, a.n_slots, bounds::kWeightSlot)) break;
         const double2 v = part[(J.tile_base + t + j) * C::kQTile + l];
         sw += v.x;
         swz += v.y;
@@ -700,6 +705,7 @@ SKArgs single_job(const aidw_grid *g, const float *qx, const float *qy, long lon
     a.n_jobs = 1;
     a.U = J.T * J.D;
     a.G = std::max(1LL, std::min(G_max, a.U));
+    a.n_slots = J.T + a.G;
     a.total_q = nq;
     a.status = &g->dev->status;
     return a;
@@ -808,7 +814,7 @@ aidw_status weight_launch(const aidw_grid *g, const float *qx, const float *qy,
 aidw_status weight_launch_batch(const WJob *jobs, int n_jobs, long long total_u,
                                 long long total_q, bool fp64, void *part, long long G,
                                 const long long *bounds, int *status, int *fail, int device,
-                                cudaStream_t s)
+                                cudaStream_t s, long long n_slots)
 {
     if (total_u <= 0 || total_q <= 0) return AIDW_OK;
     SKArgs a;
@@ -819,6 +825,7 @@ aidw_status weight_launch_batch(const WJob *jobs, int n_jobs, long long total_u,
     a.G = std::max<long long>(1, std::min<long long>(G, total_u));
     a.bounds = a.G == G ? bounds : nullptr;
     a.total_q = total_q;
+    a.n_slots = n_slots;
     a.status = status;
     a.fail = fail;
     (void)device;

@@ -1,7 +1,8 @@
 """The bounds-checked build (libaidw_checked.so): with no GPU memory checker
 available, the kernels of that build test every index they compute against
 the array it indexes (cells, cell heads, scatter and fix-up destinations,
-kNN ring segments, weighting tile copies) and count the failures.  A child
+kNN ring segments, weighting tile copies and partial-sum slots) and count
+the failures.  A child
 process runs a spread of workloads through it - ragged and clustered grids
 at several cell widths, a tiny grid, queries far outside the data, k from 1
 to 32, both precisions, the local form, pieces of weighting tiles, a batch,
