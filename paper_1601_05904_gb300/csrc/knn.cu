@@ -290,6 +290,15 @@ __global__ void __launch_bounds__(kKnnMaxThreads, knn_min_blocks(F64, KMAX))
     }
     D kth = DistT<F64>::inf();
     int kthi = 0x7fffffff;
+    // float32 path: the list as 64-bit keys (bits of d^2 << 32 | index).  A
+    // non-negative float32 orders like its bit pattern, so one unsigned
+    // compare of two keys is the (d^2, index) order; sentinels are key 0
+    // below lo and the key of (+inf, INT_MAX) above.
+    constexpr unsigned long long kEmptyKey = (0x7f800000ull << 32) | 0x7fffffffull;
+    unsigned long long kk[KMAX];
+#pragma unroll
+    for (int j = 0; j < KMAX; ++j) kk[j] = j < lo ? 0ull : kEmptyKey;
+    unsigned long long kth_key = kEmptyKey;
     long long found = 0;
     int L0 = -1;  // paper rule: the first level whose block holds k points
 
@@ -337,24 +346,43 @@ __global__ void __launch_bounds__(kKnnMaxThreads, knn_min_blocks(F64, KMAX))
                 if (s + 1 < b) nxt = P4[s + 1];
                 const int pidx = __float_as_int(p.w);
                 const D d2 = DistT<F64>::d2(qx, qy, p.x, p.y);
-                if (d2 < kth || (d2 == kth && pidx < kthi)) {
-                    // replace the k-th and bubble the candidate down to its
-                    // place.  Once it stops, no later step swaps, so the exit
-                    // test may be skipped on some steps: it is taken on every
-                    // second step for up to 16 slots and every fourth for 32
-                    // (measured at 1M: on every step, k = 10 0.70 vs 0.57 ms;
-                    // for 32 slots on every step, 2x slower; never, 1.2-1.5x
-                    // slower at k = 20..32).  While the list fills, the
-                    // candidate passes every empty (+inf) slot above its
-                    // place; a separate fill branch that starts it at the
-                    // first empty slot was slower (uniform / clustered k = 10:
-                    // 0.526 / 0.955 -> 0.685 / 1.087 ms: divergence) and made
-                    // the 24- and 32-slot forms spill.  An insertion without
-                    // a chain (rank from independent compares, then every
-                    // slot above it shifted by independent selects) was
-                    // slower for 24 and 32 slots (clustered k = 24 / 32,
-                    // uniform k = 32: 1.81 / 2.56 / 1.67 -> 2.59 / 3.91 /
-                    // 2.49 ms): the bubble's early exit saves more.
+                // A candidate that beats the k-th replaces it and bubbles
+                // down to its place.  Once it stops, no later step swaps, so
+                // the exit test may be skipped on some steps: it is taken on
+                // every second step for up to 16 slots and every fourth for
+                // 32 (measured at 1M: on every step, k = 10 0.70 vs 0.57 ms;
+                // for 32 slots on every step, 2x slower; never, 1.2-1.5x
+                // slower at k = 20..32).  The float32 path compares and moves
+                // one 64-bit key per slot instead of a (d^2, index) pair:
+                // kNN ms at 1M, uniform k = 10 / clustered k = 24, 32 /
+                // uniform k = 32: 0.525 / 1.81, 2.57 / 1.67 -> 0.470 / 1.55,
+                // 2.15 / 1.35.  While the list fills, the candidate passes
+                // every empty slot above its place; a separate fill branch
+                // that starts it at the first empty slot was slower (uniform
+                // / clustered k = 10: 0.526 / 0.955 -> 0.685 / 1.087 ms:
+                // divergence) and made the 24- and 32-slot forms spill.  An
+                // insertion without a chain (rank from independent compares,
+                // then every slot above it shifted by independent selects)
+                // was slower for 24 and 32 slots (clustered k = 24 / 32,
+                // uniform k = 32: 1.81 / 2.56 / 1.67 -> 2.59 / 3.91 / 2.49
+                // ms): the bubble's early exit saves more.
+                if (!F64) {
+                    const unsigned long long key =
+                        ((unsigned long long)__float_as_uint((float)d2) << 32) | (unsigned)pidx;
+                    if (key < kth_key) {
+                        kk[KMAX - 1] = key;
+#pragma unroll
+                        for (int j = KMAX - 1; j > 0; --j) {
+                            const bool sw = kk[j] < kk[j - 1];
+                            if ((j & (KMAX <= 16 ? 1 : 3)) == 0 && !sw) break;
+                            const unsigned long long t = kk[j], u = kk[j - 1];
+                            kk[j] = sw ? u : t;
+                            kk[j - 1] = sw ? t : u;
+                        }
+                        kth_key = kk[KMAX - 1];
+                        kth = (D)__uint_as_float((unsigned)(kth_key >> 32));
+                    }
+                } else if (d2 < kth || (d2 == kth && pidx < kthi)) {
                     kd[KMAX - 1] = d2;
                     ki[KMAX - 1] = pidx;
 #pragma unroll
@@ -385,6 +413,14 @@ __global__ void __launch_bounds__(kKnnMaxThreads, knn_min_blocks(F64, KMAX))
         if (found >= k &&
             block_is_final(eb, __int2float_rd(L), full_l, full_r, full_b, full_t, kth))
             break;
+    }
+
+    if (!F64) {
+#pragma unroll
+        for (int j = 0; j < KMAX; ++j) {
+            kd[j] = j < lo ? -DistT<F64>::inf() : (D)__uint_as_float((unsigned)(kk[j] >> 32));
+            ki[j] = j < lo ? -1 : (int)(unsigned)(kk[j] & 0xffffffffull);
+        }
     }
 
     // Eq. 3 (r_obs), Eq. 2 (r_exp, possibly with an explicit area), Eq. 4-6.
