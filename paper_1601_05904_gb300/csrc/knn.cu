@@ -348,15 +348,23 @@ __global__ void __launch_bounds__(kKnnMaxThreads, knn_min_blocks(F64, KMAX))
                 const D d2 = DistT<F64>::d2(qx, qy, p.x, p.y);
                 // A candidate that beats the k-th replaces it and bubbles
                 // down to its place.  Once it stops, no later step swaps, so
-                // the exit test may be skipped on some steps: it is taken on
-                // every second step for up to 16 slots and every fourth for
-                // 32 (measured at 1M: on every step, k = 10 0.70 vs 0.57 ms;
-                // for 32 slots on every step, 2x slower; never, 1.2-1.5x
-                // slower at k = 20..32).  The float32 path compares and moves
-                // one 64-bit key per slot instead of a (d^2, index) pair:
-                // kNN ms at 1M, uniform k = 10 / clustered k = 24, 32 /
-                // uniform k = 32: 0.525 / 1.81, 2.57 / 1.67 -> 0.470 / 1.55,
-                // 2.15 / 1.35.  While the list fills, the candidate passes
+                // the exit test may be skipped on some steps.  The float32
+                // path compares and moves one 64-bit key per slot instead of
+                // a (d^2, index) pair (kNN ms at 1M, uniform k = 10 /
+                // clustered k = 24, 32 / uniform k = 32: 0.525 / 1.81, 2.57 /
+                // 1.67 -> 0.470 / 1.55, 2.15 / 1.35 with the exit test on
+                // every second step up to 16 slots and every fourth for 24
+                // and 32) and takes the test on every fourth step up to 16
+                // slots and every eighth for 24 and 32: 0.437 / 1.47, 2.04 /
+                // 1.27 (every fourth for all: 0.438 / 1.55, 2.15 / 1.35;
+                // every eighth for all: 0.461 / 1.48, 2.04 / 1.27; every
+                // sixteenth for 24 and 32: 1.56, 2.12 / 1.35; every second
+                // for 24 and 32: 1.98, 2.91 / 1.89).  The float64 path keeps
+                // the pair, with the test on every second step up to 16
+                // slots and every fourth for 32 (with pairs, measured at 1M:
+                // on every step, k = 10 0.70 vs 0.57 ms; for 32 slots on
+                // every step, 2x slower; never, 1.2-1.5x slower at k =
+                // 20..32).  While the list fills, the candidate passes
                 // every empty slot above its place; a separate fill branch
                 // that starts it at the first empty slot was slower (uniform
                 // / clustered k = 10: 0.526 / 0.955 -> 0.685 / 1.087 ms:
@@ -374,7 +382,7 @@ __global__ void __launch_bounds__(kKnnMaxThreads, knn_min_blocks(F64, KMAX))
 #pragma unroll
                         for (int j = KMAX - 1; j > 0; --j) {
                             const bool sw = kk[j] < kk[j - 1];
-                            if ((j & (KMAX <= 16 ? 1 : 3)) == 0 && !sw) break;
+                            if ((j & (KMAX <= 16 ? 3 : 7)) == 0 && !sw) break;
                             const unsigned long long t = kk[j], u = kk[j - 1];
                             kk[j] = sw ? u : t;
                             kk[j - 1] = sw ? t : u;
