@@ -336,8 +336,8 @@ def stage_rooflines(stage, n_data, n_query, n_cells, hbm_gbs):
                       "launches": k_l,
                       "note": "bound by the SM, not by memory: one thread per query "
                               "walks its own cells and sorts its own candidates, so a "
-                              "warp instruction runs on 11.3 of 32 lanes on average; ncu "
-                              "at 1M: issue 66 % active, ALU pipe 68 % (top-k compares "
+                              "warp instruction runs on 11.7 of 32 lanes on average; ncu "
+                              "at 1M: issue 58 % active, ALU pipe 66 % (top-k compares "
                               "and selects), 4 % of L2 and 1 % of DRAM throughput"}
     return out
 
