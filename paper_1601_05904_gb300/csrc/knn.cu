@@ -200,7 +200,11 @@ __device__ __forceinline__ float decay_power_f32(float mu, const float (&a)[5])
 // k = 32 1.690, 512-job build + kNN 29.15; (2, 2, 1, 1): 0.667, 0.939/1.199/
 // 1.951/2.666, 1.690, 28.1; (2, 2, 2, 2): 0.546, 0.931/1.018/1.948/2.668,
 // 1.689, 26.9.  Three blocks (80 registers) spill.  The float64 path is
-// left free (capping its 32-slot form spills heavily).
+// left free (capping its 32-slot form spills heavily).  With 64-bit keys
+// and the exit test on every eighth step the 32-slot form spills 52 bytes
+// (68 bytes of reloads, from L1) at 128 registers and is still the fastest
+// measured form (clustered k = 32 at 1M: 2.04 ms, against 2.15 ms with the
+// test on every fourth step and no spill).
 constexpr int kKnnMinBlocks32 = 2, kKnnMinBlocks24 = 2, kKnnMinBlocks16 = 2,
               kKnnMinBlocks8 = 2;
 constexpr int knn_min_blocks(bool f64, int kmax)
