@@ -648,7 +648,9 @@ aidw_status launch(SKArgs a, void *part, cudaStream_t s)
 // Pieces per weighting tile (as a shift) for one job of n_data points and T
 // query tiles on at most G_max CTAs: the shift whose largest CTA share, in
 // points, is smallest, each unit charged kUnitCost points more for its
-// barrier wait, copy issue and chunk folds.  Whole tiles unless the point
+// barrier wait, copy issue and chunk folds (8: the fit of the measured
+// 51,200-point step, 0.853 ms with 512-point pieces against 0.838 with
+// 256, is about 6).  Whole tiles unless the point
 // set is too small to give every CTA several of them (at n = m = 10,240:
 // 50 whole-tile units for 304 CTAs, against 800 units of 128 points).
 // AIDW_WEIGHT_PIECES=s (0..4) fixes the shift, for measurement.
@@ -662,7 +664,7 @@ int piece_shift_for(long long n_data, long long T, long long G_max)
     }();
     if (!f32_split().pieces) return 0;  // this split runs whole tiles only
     if (forced >= 0) return forced;
-    constexpr double kUnitCost = 16.0;
+    constexpr double kUnitCost = 8.0;
     int best = 0;
     double best_cost = 0.0;
     for (int sh = 0; sh <= kMaxPieceShift; ++sh) {
